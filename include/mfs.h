@@ -1,0 +1,187 @@
+/*
+ * mfs.h -- C ABI of the GB300 library for the method of fundamental solutions (MFS)
+ * with lubrication-adapted image systems for rigid Stokes spheres
+ * (Broms, Barnett, Tornberg, arXiv 2407.03343).
+ *
+ * The library solves the resistance problem of Sec. 1 (eq. stokeseq, eq. bc): P equal
+ * rigid spheres with prescribed translational velocities v_k and angular velocities
+ * omega_k, optionally in a background flow u_inf, for the disturbance flow
+ *     u(x) = sum_k sum_alpha S(x - y^S) f + R(x - y^R) t + D(x - y^D) d      (eq. lin_comb)
+ * represented by Stokeslets S on an interior proxy sphere of radius R_p (Sec. 2.1) and
+ * Stokeslet/rotlet/potential-dipole triples on the image line of every near contact
+ * (Sec. 2.3, Sec. 5.1).  Collocation in the least-squares sense at the surface nodes
+ * is solved with one-body right preconditioning (Sec. 2.2, eq. resistance) and GMRES;
+ * forces and torques follow from the strengths (Sec. 2.3 remark).
+ *
+ * Conventions (all calls):
+ *  - Every array argument is a HOST pointer owned by the caller unless the function
+ *    name ends in _device, in which case it is a device pointer on the context's GPU.
+ *    Inputs are copied before the call returns; nothing is retained.
+ *  - Coordinates are (x, y, z) triples, row-major: element 3*i + c.
+ *  - Calls on a context must follow set_spheres -> build -> set_rigid_velocities (any
+ *    time after set_spheres) -> solve -> get_* ; an out-of-order call returns
+ *    MFS_ERR_STATE and changes nothing.
+ *  - A context is used by one host thread at a time.  Any failure leaves the context
+ *    usable, and mfs_last_error() describes it.
+ *  - Force sign: F = sum f is the force the sphere exerts on the fluid (Sec. 2.3 remark),
+ *    so a sphere translating with U alone has F = +6 pi mu a U.
+ *  - All work runs on the context's CUDA stream; calls are synchronous with respect
+ *    to the host (they return after the stream has drained) unless stated otherwise.
+ */
+#ifndef MFS_H
+#define MFS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfs_ctx mfs_ctx;   /* opaque; owns all device memory it allocates */
+
+typedef enum {
+  MFS_OK = 0,
+  MFS_ERR_ARG = -1,            /* null pointer, size out of range, bad parameter */
+  MFS_ERR_GEOMETRY = -2,       /* overlapping or touching spheres */
+  MFS_ERR_UNSUPPORTED = -3,    /* e.g. unequal radii */
+  MFS_ERR_STATE = -4,          /* call out of order */
+  MFS_ERR_NOT_CONVERGED = -5,  /* GMRES / refinement hit its limit; outputs hold the best iterate */
+  MFS_ERR_NUMERIC = -6,        /* NaN/Inf or Krylov breakdown */
+  MFS_ERR_OOM = -7,            /* device or host allocation failed */
+  MFS_ERR_CUDA = -8,           /* a CUDA / cuSOLVER call failed */
+  MFS_ERR_TIMEOUT = -9         /* a bounded device wait ran out */
+} mfs_status;
+
+/* Precision of the solve and of the single-step entry points:
+ *  MFS_FP64   native FP64 everywhere.
+ *  MFS_MIXED  FP64 GMRES, FP64 pseudo-inverse factors; the pair sums of steps 2+3 run in
+ *             double-float arithmetic (pairs of FP32 values, ~2^-46 relative) on the FP32
+ *             pipes, which this GPU executes 74x faster than FP64.
+ *  MFS_FP32   FP32 inner GMRES on an all-FP32 operator with FP64 iterative refinement;
+ *             converges only when B_k^+ amplifies by well under 1/eps_FP32, i.e. not with
+ *             images and the paper's truncation 5e-12 (returns MFS_ERR_NOT_CONVERGED). */
+enum { MFS_FP64 = 0, MFS_MIXED = 1, MFS_FP32 = 2 };
+
+/* Discretisation parameters (Sec. 2.1, Sec. 2.3, Sec. 5.1, App. A.1).
+ * Defaults (mfs_default_params): the paper's coarse choice N = 686, R_p = 0.63,
+ * M0 = 823 (~1.2 N), Delta = 0.05, alpha = 6, beta1 = pi/5, beta2 = pi/60,
+ * eps_trunc = 5e-12, n_im rule ceil(-8.72 log10(delta) - 6.15) for delta < 0.15,
+ * capped at 20, left row scaling on, viscosity 1. */
+typedef struct {
+  int n_proxy;          /* N: proxy Stokeslets per sphere on radius r_proxy * a */
+  double r_proxy;       /* R_p, in radius units, 0 < R_p < 1/(1 + delta_offset) */
+  int m_basic;          /* M0: basic collocation nodes per sphere (Fibonacci grid) */
+  double delta_offset;  /* Delta in eq. tj */
+  int alpha1, alpha2;   /* cap upsampling, eq. colloc_nbr: M_cap = alpha * 3 * n_im */
+  double beta1, beta2;  /* cap half-angles (radians), eq. thetacap */
+  double eps_trunc;     /* singular values below eps_trunc * sigma_max are dropped */
+  double nim_a, nim_b, nim_cut; /* eq. image_est: n_im = ceil(-nim_a log10(delta) - nim_b) if delta < nim_cut */
+  int nim_max;          /* cap on n_im (20) */
+  int nim_fixed;        /* >= 0: every contact with delta < nim_cut gets exactly this n_im */
+  int left_precond;     /* 1: rows scaled by sqrt(area weight) (Sec. 5.1 remark left-precond) */
+  double visc;          /* viscosity mu */
+} mfs_params;
+
+/* GMRES / refinement options (precision as above).  Every mode re-evaluates the residual
+ * ||W b - G_hat mu|| / ||W b|| with its FP64-accurate operator after each GMRES pass and
+ * solves the correction equation again (iterative refinement) until it is <= tol.
+ * Defaults: MIXED, tol 1e-6 (Sec. 3, Sec. 5), max_iter 2000, restart 300,
+ * max_refine 20, inner_tol 1e-4 (MFS_FP32 inner solves only). */
+typedef struct {
+  int precision;
+  double tol;
+  int max_iter;     /* total inner GMRES iterations over all refinements */
+  int restart;      /* GMRES restart length m */
+  int max_refine;   /* outer refinement steps (MIXED) */
+  double inner_tol; /* relative residual reduction asked of each inner solve (MIXED) */
+} mfs_solve_opts;
+
+typedef struct {
+  int iters;           /* GMRES iterations (all refinements) */
+  int refinements;     /* outer FP64 residual evaluations after the first */
+  double rel_residual; /* final ||W b - G_hat mu|| / ||W b||, evaluated in FP64 */
+  double seconds;      /* wall time of the call */
+  int converged;       /* 1 if rel_residual <= tol */
+} mfs_solve_info;
+
+typedef struct {
+  int P;              /* spheres */
+  int n_contacts;     /* near contacts that received images */
+  int n_colloc;       /* total collocation nodes, sum_k M^(k); operator size is 3*n_colloc */
+  int n_proxy_total;  /* P * N */
+  int n_image_nodes;  /* total image nodes; each carries S, R and D (3 vector sources) */
+  int n_unknowns;     /* 3 * sum_k N^(k) = 3 * (n_proxy_total + 3 * n_image_nodes) */
+  int n_factors;      /* distinct one-body factors (shared basic block + one per contact sphere) */
+  long long pairs_fp; /* (target node, vector source) pairs of one operator apply, self blocks excluded;
+                         an image S+R+D triple counts as 3 */
+} mfs_sizes_t;
+
+void mfs_default_params(mfs_params* p);
+void mfs_default_solve_opts(mfs_solve_opts* o);
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t to run on,
+ * or NULL for a stream the context creates and owns. */
+mfs_status mfs_create(mfs_ctx** out, int device, void* cuda_stream);
+void mfs_destroy(mfs_ctx* ctx);
+/* Message of the last failure on this context ("" if none).  Owned by the context. */
+const char* mfs_last_error(const mfs_ctx* ctx);
+
+/* P spheres: centres (P*3), radii (P).  All radii must be equal (MFS_ERR_UNSUPPORTED
+ * otherwise, Sec. 2.1 fixes identical spheres); spheres must not touch or overlap
+ * (MFS_ERR_GEOMETRY).  Invalidates any previous build. */
+mfs_status mfs_set_spheres(mfs_ctx* ctx, int P, const double* centres, const double* radii);
+
+/* Rigid-body boundary data of eq. bc: v (P*3), omega (P*3). */
+mfs_status mfs_set_rigid_velocities(mfs_ctx* ctx, const double* v, const double* omega);
+mfs_status mfs_set_rigid_velocities_device(mfs_ctx* ctx, const double* d_v, const double* d_omega);
+
+/* Background flow u_inf(x) = U + E x + Omega x x subtracted in eq. bc (Sec. 4, Ex. 2).
+ * Each pointer may be NULL (term absent): U (3), E (3*3 row-major), Omega (3). */
+mfs_status mfs_set_background_flow(mfs_ctx* ctx, const double* U, const double* E, const double* Omega);
+
+/* Discretise (contacts, image lines, caps, weights) and compute every distinct
+ * one-body truncated pseudo-inverse B_k^+ = V Sigma^+ U^T in FP64 on the GPU
+ * (Sec. 2.2, Sec. 2.3, Sec. 5.1).  NULL params = defaults. */
+mfs_status mfs_build(mfs_ctx* ctx, const mfs_params* params);
+mfs_status mfs_sizes(const mfs_ctx* ctx, mfs_sizes_t* out);
+
+/* Solve eq. resistance for the current boundary data, then form lambda = B^+ mu in FP64.
+ * NULL opts = defaults; info may be NULL.  MFS_ERR_NOT_CONVERGED still leaves the
+ * best iterate's outputs available. */
+mfs_status mfs_solve(mfs_ctx* ctx, const mfs_solve_opts* opts, mfs_solve_info* info);
+
+/* Forces and torques on each sphere (Sec. 2.3 remark): F (P*3), T (P*3). */
+mfs_status mfs_get_forces_torques(mfs_ctx* ctx, double* F, double* T);
+mfs_status mfs_get_forces_torques_device(mfs_ctx* ctx, double* d_F, double* d_T);
+
+/* Disturbance velocity u(x) = G(x) lambda at n arbitrary points x (n*3) -> u (n*3),
+ * FP64; points inside a sphere get the (meaningless) continuation. */
+mfs_status mfs_eval_velocity(mfs_ctx* ctx, int n, const double* x, double* u);
+
+/* Strengths lambda (n_unknowns) in the library's order: per sphere k, first the N proxy
+ * Stokeslets (3 each), then per image node its Stokeslet f, rotlet t and dipole d
+ * (9 values).  pos (n_vector_sources*3) and type (0 = S, 1 = R, 2 = D) may be NULL. */
+mfs_status mfs_get_strengths(mfs_ctx* ctx, double* lambda, double* pos, int* type);
+
+/* Collocation nodes (n_colloc*3), area weights (n_colloc) and owner sphere (n_colloc);
+ * per sphere: M0 basic nodes, then for each partner in ascending index order its two caps.
+ * Any pointer may be NULL. */
+mfs_status mfs_get_collocation(mfs_ctx* ctx, double* x, double* w, int* owner);
+
+/* ---- single steps of the hot path, for checking each against a reference ----
+ * Vectors in row space have length 3*n_colloc (node-major, xyz), vectors in source
+ * space have length n_unknowns in the strength order above.  All host pointers. */
+
+/* W b: scaled boundary data at the collocation nodes (eq. lq2). */
+mfs_status mfs_get_rhs(mfs_ctx* ctx, double* wb);
+/* out = G_hat mu (eq. resistance) by the three steps of Sec. 2.2 with steps 2 and 3
+ * fused (self blocks skipped), with the operator of the given precision mode. */
+mfs_status mfs_apply_operator(mfs_ctx* ctx, int precision, const double* mu, double* out);
+/* Step 1 alone: lambda_hat = B_k^+ mu_k for every sphere (eq. transform). */
+mfs_status mfs_apply_precond(mfs_ctx* ctx, int precision, const double* mu, double* lambda_hat);
+/* Steps 2+3 alone: out = mu + W_k sum_{k' != k} G^(kk') lambda_hat_k' (eq. uAll). */
+mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat,
+                           const double* mu, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFS_H */

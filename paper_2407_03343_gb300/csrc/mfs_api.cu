@@ -1,0 +1,1137 @@
+// C ABI of libmfs: context, build (discretisation + one-body factorisation), GMRES drivers.
+//
+// Solve (Sec. 2.2): GMRES on G_hat mu = W b (eq. resistance) with the three-step apply
+//   step 1  lambda_hat_k = V_k (Sigma_k^+ (U_k^T mu_k))      batched GEMV, eq. transform
+//   step 2+3  out = mu + W sum_{k' != k} G^(kk') lambda_hat   pairs kernel, eq. uAll
+// then lambda = B^+ mu and forces/torques (Sec. 2.3 remark).
+// MFS_FP64 runs GMRES in FP64 with the native FP64 pair kernel.  MFS_MIXED runs the same
+// FP64 GMRES but evaluates the pair sums (about 90% of the work) in double-float arithmetic
+// on the FP32 pipes, because FP64 throughput on this GPU is 1/74 of FP32, while plain FP32
+// pair sums cannot carry the cancellation in G B^+ mu (B^+ truncated at 5e-12 amplifies by
+// up to ~1e11).  MFS_FP32 runs FP32 inner GMRES on an all-FP32 operator with FP64 iterative
+// refinement; it converges only when the one-body blocks are moderately conditioned.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <string>
+#include <vector>
+
+#include <cusolverDn.h>
+
+#include "mfs_internal.h"
+
+using namespace mfs;
+
+namespace {
+
+constexpr int kTileTargets = 512;  // 128 threads x 4 nodes, must match the pairs kernel
+constexpr double kPi = 3.14159265358979323846;
+
+inline int pad4(int x) { return (x + 3) & ~3; }
+
+struct Factor {
+  int m = 0, ncol = 0, rank = 0, ldA = 0, ldV = 0;
+  double* A64 = nullptr;  // rank x ldA  (Sigma^+ U^T)
+  double* V64 = nullptr;  // ncol x ldV  (V)
+  float* A32 = nullptr;
+  float* V32 = nullptr;
+};
+
+// keep[i] is the SVD column index of the i-th retained singular triplet
+__global__ void pack_A_kernel(int r, int m, int ld, const double* __restrict__ U, const double* __restrict__ S,
+                              const int* __restrict__ keep, double* __restrict__ A64, float* __restrict__ A32) {
+  long long tot = (long long)r * ld;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(id / ld), j = (int)(id % ld);
+    int col = keep[i];
+    double v = j < m ? U[(long long)col * m + j] / S[col] : 0.0;
+    A64[id] = v;
+    A32[id] = (float)v;
+  }
+}
+
+// VT is the column-major ncol x ncol matrix V^T returned by the SVD: V(row, i) = VT[row * ncol + i]
+__global__ void pack_V_kernel(int ncol, int r, int ld, const double* __restrict__ VT, const int* __restrict__ keep,
+                              double* __restrict__ V64, float* __restrict__ V32) {
+  long long tot = (long long)ncol * ld;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    int row = (int)(id / ld), i = (int)(id % ld);
+    double v = i < r ? VT[(long long)row * ncol + keep[i]] : 0.0;
+    V64[id] = v;
+    V32[id] = (float)v;
+  }
+}
+
+}  // namespace
+
+struct mfs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  int state = 0;        // 0 empty, 1 spheres set, 2 built
+  bool have_bc = false;
+  bool solved = false;
+  bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel
+  int P = 0;
+  double a = 1.0;
+  std::vector<double> centres;
+  std::vector<double> bg = std::vector<double>(15, 0.0);
+  HostDisc hd;
+  cusolverDnHandle_t solver = nullptr;
+
+  // device memory owned by the current build
+  std::vector<void*> allocs;
+  TargetSet tg;
+  SourceSet src;
+  double* d_colloc_abs = nullptr;
+  int* d_owner = nullptr;
+  double* d_sqrtw = nullptr;
+  std::vector<Factor> factors;
+  GemvBatch<float> gA32, gV32;
+  GemvBatch<double> gA64, gV64;
+  long long tmp_len = 0;
+  int n = 0;              // operator size 3 * n_colloc
+  long long n_unk = 0;
+  double *d_v = nullptr, *d_om = nullptr, *d_wb = nullptr, *d_mu = nullptr, *d_r = nullptr, *d_w64 = nullptr;
+  double *d_tmp64 = nullptr, *d_lh64 = nullptr, *d_lam = nullptr, *d_F = nullptr, *d_T = nullptr;
+  float *d_tmp32 = nullptr, *d_lh32 = nullptr, *d_in32 = nullptr, *d_out32 = nullptr, *d_mu32 = nullptr;
+  // Krylov workspace (lazily sized)
+  void* d_basis = nullptr;
+  size_t basis_bytes = 0;
+  double* d_partial = nullptr;
+  double* d_h = nullptr;
+  int nblk = 1;
+
+  mfs_status fail(mfs_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  template <typename T>
+  T* dalloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void free_build() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    factors.clear();
+    tg = TargetSet();
+    src = SourceSet();
+    d_basis = nullptr;
+    basis_bytes = 0;
+    solved = false;
+  }
+};
+
+#define CUDA_TRY(ctx, x)                                                                  \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess) return (ctx)->fail(MFS_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define CUSOLVER_TRY(ctx, x)                                                              \
+  do {                                                                                    \
+    cusolverStatus_t s_ = (x);                                                            \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                    \
+      return (ctx)->fail(MFS_ERR_CUDA, std::string(#x) + ": cusolver status " + std::to_string((int)s_)); \
+  } while (0)
+#define ALLOC_TRY(ctx, ptr, T, count)                                                     \
+  do {                                                                                    \
+    (ptr) = (ctx)->dalloc<T>(count);                                                      \
+    if (!(ptr)) return (ctx)->fail(MFS_ERR_OOM, "device allocation failed: " #ptr);      \
+  } while (0)
+#define CHECK_LAUNCH(ctx) CUDA_TRY(ctx, cudaGetLastError())
+
+namespace {
+
+template <typename T>
+mfs_status upload(mfs_ctx* c, T*& dst, const std::vector<T>& v) {
+  ALLOC_TRY(c, dst, T, v.size());
+  if (!v.empty()) CUDA_TRY(c, cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return MFS_OK;
+}
+
+// ------------------------------------------------------------------ operator pieces
+template <typename T> struct Ops;
+template <> struct Ops<float> {
+  static const GemvBatch<float>& A(mfs_ctx* c) { return c->gA32; }
+  static const GemvBatch<float>& V(mfs_ctx* c) { return c->gV32; }
+  static float* tmp(mfs_ctx* c) { return c->d_tmp32; }
+  static float* lh(mfs_ctx* c) { return c->d_lh32; }
+};
+template <> struct Ops<double> {
+  static const GemvBatch<double>& A(mfs_ctx* c) { return c->gA64; }
+  static const GemvBatch<double>& V(mfs_ctx* c) { return c->gV64; }
+  static double* tmp(mfs_ctx* c) { return c->d_tmp64; }
+  static double* lh(mfs_ctx* c) { return c->d_lh64; }
+};
+
+// step 1: lambda_hat = B^+ mu (two factors in turn, eq. transform)
+template <typename T>
+void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
+  launch_gemv<T>(Ops<T>::A(c), mu, Ops<T>::tmp(c), c->stream);
+  launch_gemv<T>(Ops<T>::V(c), Ops<T>::tmp(c), lam_hat, c->stream);
+}
+
+// out = G_hat mu
+template <typename T>
+void apply_op(mfs_ctx* c, const T* mu, T* out) {
+  precond<T>(c, mu, Ops<T>::lh(c));
+  if constexpr (sizeof(T) == 8) {
+    if (c->dw_pairs) {
+      launch_pairs_dw(c->tg, c->src, Ops<T>::lh(c), mu, out, c->hd.prm.visc, c->stream);
+      return;
+    }
+  }
+  launch_pairs<T>(c->tg, c->src, Ops<T>::lh(c), mu, out, c->hd.prm.visc, c->stream);
+}
+
+template <typename T>
+mfs_status ensure_krylov(mfs_ctx* c, int restart) {
+  size_t need = (size_t)(restart + 1) * (size_t)c->n * sizeof(T);
+  if (c->basis_bytes < need) {
+    if (c->d_basis) {
+      cudaFree(c->d_basis);
+      c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), c->d_basis), c->allocs.end());
+      c->d_basis = nullptr;
+    }
+    c->d_basis = c->dalloc<char>(need);
+    if (!c->d_basis) return c->fail(MFS_ERR_OOM, "device allocation failed: Krylov basis");
+    c->basis_bytes = need;
+  }
+  return MFS_OK;
+}
+
+// dot products of w with V[0..nvec) (FP64 partials) -> host h
+template <typename T>
+mfs_status dots(mfs_ctx* c, int nvec, const T* V, const T* w, double* h_dev) {
+  launch_multidot<T>(c->n, nvec, V, c->n, w, c->d_partial, c->nblk, c->stream);
+  launch_reduce_partials(nvec, c->nblk, c->d_partial, h_dev, c->stream);
+  CHECK_LAUNCH(c);
+  return MFS_OK;
+}
+
+// Restarted GMRES(m) with CGS2 Arnoldi (classical Gram-Schmidt applied twice), Givens
+// rotations and the small least-squares problem on the host in FP64 (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 6.9).  Solves op x = b from x0 = 0 and stops at
+// ||b - op x|| <= tol ||b|| (the GMRES estimate; restarts use the true residual).
+template <typename T>
+mfs_status gmres(mfs_ctx* c, const T* b, T* x, double tol, int restart, int max_iter, int& iters, double& rel) {
+  mfs_status s = ensure_krylov<T>(c, restart);
+  if (s != MFS_OK) return s;
+  const int n = c->n;
+  const int ldh = restart + 1;
+  T* V = static_cast<T*>(c->d_basis);
+  std::vector<double> H((size_t)ldh * restart), cs(restart), sn(restart), g(ldh), hb(2 * ldh + 1), y(restart);
+  double* h1 = c->d_h;
+  double* h2 = c->d_h + ldh;
+  double* hn = c->d_h + 2 * ldh;
+  double* coef = c->d_h + 3 * ldh;
+  CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(T) * n, c->stream));
+  iters = 0;
+  rel = 0.0;
+  if ((s = dots<T>(c, 1, b, b, hn)) != MFS_OK) return s;
+  double bn2 = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bn2, hn, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) return c->fail(MFS_ERR_NUMERIC, "right-hand side is not finite");
+  if (bnorm == 0.0) return MFS_OK;
+  const double one = 1.0;
+  bool first = true;
+  while (true) {
+    double beta;
+    if (first) {
+      launch_scale_copy<T>(n, b, 1.0, V, c->stream);
+      beta = bnorm;
+      first = false;
+    } else {
+      // V0 = b - op x
+      apply_op<T>(c, x, V);
+      launch_scale_copy<T>(n, V, -1.0, V, c->stream);
+      CUDA_TRY(c, cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      launch_update<T>(n, 1, b, n, coef, 1.0, V, c->stream);
+      CHECK_LAUNCH(c);
+      if ((s = dots<T>(c, 1, V, V, hn)) != MFS_OK) return s;
+      double r2 = 0;
+      CUDA_TRY(c, cudaMemcpyAsync(&r2, hn, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      beta = std::sqrt(r2);
+      rel = beta / bnorm;
+      if (!std::isfinite(beta)) return c->fail(MFS_ERR_NUMERIC, "non-finite GMRES residual");
+      if (rel <= tol || iters >= max_iter || beta == 0.0) break;
+    }
+    launch_scale_copy<T>(n, V, 1.0 / beta, V, c->stream);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j_used = 0;
+    bool done = false;
+    for (int j = 0; j < restart; ++j) {
+      T* w = V + (size_t)(j + 1) * n;
+      apply_op<T>(c, V + (size_t)j * n, w);
+      CHECK_LAUNCH(c);
+      if ((s = dots<T>(c, j + 1, V, w, h1)) != MFS_OK) return s;
+      launch_update<T>(n, j + 1, V, n, h1, -1.0, w, c->stream);
+      if ((s = dots<T>(c, j + 1, V, w, h2)) != MFS_OK) return s;
+      launch_update<T>(n, j + 1, V, n, h2, -1.0, w, c->stream);
+      if ((s = dots<T>(c, 1, w, w, hn)) != MFS_OK) return s;
+      CUDA_TRY(c, cudaMemcpyAsync(hb.data(), c->d_h, sizeof(double) * (2 * ldh + 1), cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      double* col = &H[(size_t)j * ldh];
+      for (int i = 0; i <= j; ++i) col[i] = hb[i] + hb[ldh + i];
+      const double hnext = std::sqrt(std::max(0.0, hb[2 * ldh]));
+      if (!std::isfinite(hnext)) return c->fail(MFS_ERR_NUMERIC, "non-finite value in the Arnoldi process");
+      col[j + 1] = hnext;
+      if (hnext > 0) launch_scale_copy<T>(n, w, 1.0 / hnext, w, c->stream);
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[j] = den > 0 ? col[j] / den : 1.0;
+      sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      j_used = j + 1;
+      rel = std::fabs(g[j + 1]) / bnorm;
+      if (rel <= tol || iters >= max_iter || hnext == 0.0) {
+        done = true;
+        break;
+      }
+    }
+    // y = R^{-1} g, x += V y
+    for (int i = j_used - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < j_used; ++q) t -= H[(size_t)q * ldh + i] * y[q];
+      const double diag = H[(size_t)i * ldh + i];
+      y[i] = diag != 0.0 ? t / diag : 0.0;
+    }
+    if (j_used > 0) {
+      CUDA_TRY(c, cudaMemcpyAsync(coef, y.data(), sizeof(double) * j_used, cudaMemcpyHostToDevice, c->stream));
+      launch_update<T>(n, j_used, V, n, coef, 1.0, x, c->stream);
+      CHECK_LAUNCH(c);
+    }
+    if (done) break;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
+// ||v||_2 of an FP64 device vector
+mfs_status norm64(mfs_ctx* c, const double* v, double& out) {
+  mfs_status s = dots<double>(c, 1, v, v, c->d_h + 4 * 512);
+  if (s != MFS_OK) return s;
+  double r2 = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&r2, c->d_h + 4 * 512, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  out = std::sqrt(r2);
+  return MFS_OK;
+}
+
+mfs_status check_state(mfs_ctx* c, int need) {
+  if (!c) return MFS_ERR_ARG;
+  if (c->state < need) return c->fail(MFS_ERR_STATE, need == 1 ? "spheres not set" : "discretisation not built");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return c->fail(MFS_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return MFS_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+void mfs_default_params(mfs_params* p) {
+  if (!p) return;
+  p->n_proxy = 686;
+  p->r_proxy = 0.63;
+  p->m_basic = 823;
+  p->delta_offset = 0.05;
+  p->alpha1 = 6;
+  p->alpha2 = 6;
+  p->beta1 = kPi / 5.0;
+  p->beta2 = kPi / 60.0;
+  p->eps_trunc = 5e-12;
+  p->nim_a = 8.72;
+  p->nim_b = 6.15;
+  p->nim_cut = 0.15;
+  p->nim_max = 20;
+  p->nim_fixed = -1;
+  p->left_precond = 1;
+  p->visc = 1.0;
+}
+
+void mfs_default_solve_opts(mfs_solve_opts* o) {
+  if (!o) return;
+  o->precision = MFS_MIXED;
+  o->tol = 1e-6;
+  o->max_iter = 2000;
+  o->restart = 300;
+  o->max_refine = 20;
+  o->inner_tol = 1e-4;
+}
+
+mfs_status mfs_create(mfs_ctx** out, int device, void* cuda_stream) {
+  if (!out) return MFS_ERR_ARG;
+  *out = nullptr;
+  mfs_ctx* c = new (std::nothrow) mfs_ctx();
+  if (!c) return MFS_ERR_OOM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MFS_ERR_CUDA;
+  }
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return MFS_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return MFS_OK;
+}
+
+void mfs_destroy(mfs_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  c->free_build();
+  if (c->solver) cusolverDnDestroy(c->solver);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* mfs_last_error(const mfs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+mfs_status mfs_set_spheres(mfs_ctx* c, int P, const double* centres, const double* radii) {
+  if (!c) return MFS_ERR_ARG;
+  if (P <= 0 || !centres || !radii) return c->fail(MFS_ERR_ARG, "P must be positive and arrays non-null");
+  double a = radii[0];
+  if (!(a > 0) || !std::isfinite(a)) return c->fail(MFS_ERR_ARG, "radius must be positive");
+  for (int k = 0; k < P; ++k) {
+    if (std::fabs(radii[k] - a) > 1e-12 * a) return c->fail(MFS_ERR_UNSUPPORTED, "all spheres must have the same radius");
+    for (int q = 0; q < 3; ++q)
+      if (!std::isfinite(centres[3 * k + q])) return c->fail(MFS_ERR_ARG, "non-finite centre");
+  }
+  c->free_build();
+  c->P = P;
+  c->a = a;
+  c->centres.assign(centres, centres + 3 * (size_t)P);
+  c->state = 1;
+  c->have_bc = false;
+  c->err.clear();
+  return MFS_OK;
+}
+
+mfs_status mfs_set_background_flow(mfs_ctx* c, const double* U, const double* E, const double* Om) {
+  if (!c) return MFS_ERR_ARG;
+  std::fill(c->bg.begin(), c->bg.end(), 0.0);
+  if (U) std::copy(U, U + 3, c->bg.begin());
+  if (E) std::copy(E, E + 9, c->bg.begin() + 3);
+  if (Om) std::copy(Om, Om + 3, c->bg.begin() + 12);
+  c->solved = false;
+  return MFS_OK;
+}
+
+mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
+  mfs_status s = check_state(c, 1);
+  if (s != MFS_OK) return s;
+  mfs_params p;
+  if (params) p = *params; else mfs_default_params(&p);
+  c->free_build();
+  c->state = 1;
+  HostDisc hd;
+  s = build_discretisation(c->centres.data(), c->P, c->a, p, hd, c->err);
+  if (s != MFS_OK) return s;
+  c->hd = std::move(hd);
+  HostDisc& d = c->hd;
+  const int P = d.P, N = p.n_proxy, nc = d.n_colloc(), ni = d.n_img();
+  c->n = 3 * nc;
+  c->n_unk = d.n_unknowns();
+
+  // ---- targets: positions relative to the owner centre, tiles inside one sphere
+  std::vector<float4> t32(nc);
+  std::vector<double> t64(4 * (size_t)nc), cabs(d.colloc), sw(nc);
+  std::vector<int> ts, tst, tcn;
+  for (int k = 0; k < P; ++k) {
+    for (int i = d.colloc_off[k]; i < d.colloc_off[k + 1]; ++i) {
+      double r[3];
+      for (int q = 0; q < 3; ++q) r[q] = d.colloc[3 * i + q] - d.centres[3 * k + q];
+      double w = p.left_precond ? std::sqrt(d.weight[i]) : 1.0;
+      sw[i] = w;
+      t32[i] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)w);
+      t64[4 * i] = r[0]; t64[4 * i + 1] = r[1]; t64[4 * i + 2] = r[2]; t64[4 * i + 3] = w;
+    }
+    for (int s0 = d.colloc_off[k]; s0 < d.colloc_off[k + 1]; s0 += kTileTargets) {
+      ts.push_back(k);
+      tst.push_back(s0);
+      tcn.push_back(std::min(kTileTargets, d.colloc_off[k + 1] - s0));
+    }
+  }
+  c->tg.n = nc;
+  c->tg.n_tiles = (int)ts.size();
+  if ((s = upload(c, c->tg.pos32, t32)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.pos64, t64)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.tile_sphere, ts)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.tile_start, tst)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.tile_count, tcn)) != MFS_OK) return s;
+  if ((s = upload(c, c->d_colloc_abs, cabs)) != MFS_OK) return s;
+  if ((s = upload(c, c->d_owner, d.owner)) != MFS_OK) return s;
+  if ((s = upload(c, c->d_sqrtw, sw)) != MFS_OK) return s;
+
+  // ---- sources
+  std::vector<float4> p32(N), i32(std::max(ni, 1));
+  std::vector<double> p64(4 * (size_t)N), i64(4 * (size_t)std::max(ni, 1), 0.0);
+  for (int j = 0; j < N; ++j) {
+    p32[j] = make_float4((float)d.proxy_rel[3 * j], (float)d.proxy_rel[3 * j + 1], (float)d.proxy_rel[3 * j + 2], 0.f);
+    for (int q = 0; q < 3; ++q) p64[4 * j + q] = d.proxy_rel[3 * j + q];
+    p64[4 * j + 3] = 0;
+  }
+  for (int j = 0; j < ni; ++j) {
+    int o = d.img_owner[j];
+    double r[3];
+    for (int q = 0; q < 3; ++q) r[q] = d.image[3 * j + q] - d.centres[3 * o + q];
+    i32[j] = make_float4((float)r[0], (float)r[1], (float)r[2], 0.f);
+    for (int q = 0; q < 3; ++q) i64[4 * j + q] = r[q];
+  }
+  std::vector<float> chi(3 * (size_t)P), clo(3 * (size_t)P);
+  for (int i = 0; i < 3 * P; ++i) {
+    chi[i] = (float)d.centres[i];
+    clo[i] = (float)(d.centres[i] - (double)chi[i]);
+  }
+  std::vector<int> io = d.img_owner;
+  if (io.empty()) io.push_back(0);
+  c->src.P = P;
+  c->src.N = N;
+  c->src.n_img = ni;
+  if ((s = upload(c, c->src.proxy32, p32)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.proxy64, p64)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.img32, i32)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.img64, i64)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.img_owner, io)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.unk_off, d.unk_off)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.img_off, d.img_off)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.cen_hi, chi)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.cen_lo, clo)) != MFS_OK) return s;
+  if ((s = upload(c, c->src.cen64, d.centres)) != MFS_OK) return s;
+
+  // ---- one-body factors: B_k = W_k G^(kk), thin SVD in FP64 (Golub-Kahan bidiagonalisation
+  // with implicit QR, backward stable), truncation at eps_trunc sigma_max, packing.  The
+  // distinct blocks are spread over host worker threads, each with its own stream, cuSOLVER
+  // handle and scratch, so the latency-bound parts of the SVDs overlap on the GPU.
+  const int nf = (int)d.factor_rep.size();
+  int max_m = 0, max_nc = 0;
+  for (int f = 0; f < nf; ++f) {
+    int k = d.factor_rep[f];
+    int m = 3 * (d.colloc_off[k + 1] - d.colloc_off[k]);
+    int ncol = (int)(d.unk_off[k + 1] - d.unk_off[k]);
+    if (m < ncol) return c->fail(MFS_ERR_ARG, "more unknowns than collocation equations on a sphere; raise m_basic");
+    max_m = std::max(max_m, m);
+    max_nc = std::max(max_nc, ncol);
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // geometry uploads done before workers start
+  c->factors.assign(nf, Factor());
+  const int n_workers = std::max(1, std::min(nf, 8));
+  std::mutex mtx;
+  std::string werr;
+  mfs_status wstat = MFS_OK;
+  auto worker = [&](int wid) {
+    auto fail_w = [&](mfs_status st, const std::string& msg) {
+      std::lock_guard<std::mutex> g(mtx);
+      if (wstat == MFS_OK) {
+        wstat = st;
+        werr = msg;
+      }
+    };
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail_w(MFS_ERR_CUDA, "cudaSetDevice in factor worker");
+    cudaStream_t st = nullptr;
+    cusolverDnHandle_t h = nullptr;
+    std::vector<void*> scratch;
+    auto salloc = [&](size_t bytes) -> void* {
+      void* q = nullptr;
+      if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      scratch.push_back(q);
+      return q;
+    };
+    auto cleanup = [&]() {
+      if (st) cudaStreamSynchronize(st);
+      for (void* q : scratch) cudaFree(q);
+      if (h) cusolverDnDestroy(h);
+      if (st) cudaStreamDestroy(st);
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnSetStream(h, st) != CUSOLVER_STATUS_SUCCESS) {
+      cudaGetLastError();
+      cleanup();
+      return fail_w(MFS_ERR_CUDA, "factor worker: stream or cuSOLVER handle creation failed");
+    }
+    int lwork = 0;
+    if (cusolverDnDgesvd_bufferSize(h, max_m, max_nc, &lwork) != CUSOLVER_STATUS_SUCCESS) {
+      cleanup();
+      return fail_w(MFS_ERR_CUDA, "cusolverDnDgesvd_bufferSize failed");
+    }
+    double* dB = (double*)salloc(sizeof(double) * (size_t)max_m * max_nc);
+    double* dU = (double*)salloc(sizeof(double) * (size_t)max_m * max_nc);
+    double* dVT = (double*)salloc(sizeof(double) * (size_t)max_nc * max_nc);
+    double* dS = (double*)salloc(sizeof(double) * max_nc);
+    double* drw = (double*)salloc(sizeof(double) * max_nc);
+    double* dwork = (double*)salloc(sizeof(double) * (size_t)lwork);
+    int* dinfo = (int*)salloc(sizeof(int));
+    double* dxr = (double*)salloc(sizeof(double) * (size_t)max_m);
+    double* dsw = (double*)salloc(sizeof(double) * ((size_t)max_m / 3 + 1));
+    double* dyr = (double*)salloc(sizeof(double) * (size_t)max_nc);
+    int* dty = (int*)salloc(sizeof(int) * ((size_t)max_nc / 3 + 1));
+    int* dkeep = (int*)salloc(sizeof(int) * (size_t)max_nc);
+    if (!dB || !dU || !dVT || !dS || !drw || !dwork || !dinfo || !dxr || !dsw || !dyr || !dty || !dkeep) {
+      cleanup();
+      return fail_w(MFS_ERR_OOM, "device allocation failed: factorisation scratch");
+    }
+    std::vector<double> hS(max_nc);
+    for (int f = wid; f < nf; f += n_workers) {
+      {
+        std::lock_guard<std::mutex> g(mtx);
+        if (wstat != MFS_OK) break;
+      }
+      const int k = d.factor_rep[f];
+      const int m_nodes = d.colloc_off[k + 1] - d.colloc_off[k];
+      const int m = 3 * m_nodes;
+      const int ncol = (int)(d.unk_off[k + 1] - d.unk_off[k]);
+      const int n_src = ncol / 3;
+      // rows: collocation nodes of k relative to c_k; columns: strength order (proxies, then S, R, D per image node)
+      std::vector<double> xr(3 * (size_t)m_nodes), swk(m_nodes), yr(3 * (size_t)n_src);
+      std::vector<int> ty(n_src);
+      for (int i = 0; i < m_nodes; ++i) {
+        int gi = d.colloc_off[k] + i;
+        for (int q = 0; q < 3; ++q) xr[3 * i + q] = d.colloc[3 * gi + q] - d.centres[3 * k + q];
+        swk[i] = sw[gi];
+      }
+      for (int j = 0; j < N; ++j) {
+        for (int q = 0; q < 3; ++q) yr[3 * j + q] = d.proxy_rel[3 * j + q];
+        ty[j] = 0;
+      }
+      for (int j = d.img_off[k]; j < d.img_off[k + 1]; ++j) {
+        int base = N + 3 * (j - d.img_off[k]);
+        for (int t = 0; t < 3; ++t) {
+          for (int q = 0; q < 3; ++q) yr[3 * (base + t) + q] = d.image[3 * j + q] - d.centres[3 * k + q];
+          ty[base + t] = t;
+        }
+      }
+      cudaError_t e1 = cudaMemcpyAsync(dxr, xr.data(), xr.size() * 8, cudaMemcpyHostToDevice, st);
+      cudaError_t e2 = cudaMemcpyAsync(dsw, swk.data(), swk.size() * 8, cudaMemcpyHostToDevice, st);
+      cudaError_t e3 = cudaMemcpyAsync(dyr, yr.data(), yr.size() * 8, cudaMemcpyHostToDevice, st);
+      cudaError_t e4 = cudaMemcpyAsync(dty, ty.data(), ty.size() * 4, cudaMemcpyHostToDevice, st);
+      if (e1 || e2 || e3 || e4) {
+        fail_w(MFS_ERR_CUDA, "upload of self-block geometry failed");
+        break;
+      }
+      launch_assemble_self(d, k, dxr, dsw, dyr, dty, n_src, dB, m, st);
+      int lw = 0;
+      cusolverDnDgesvd_bufferSize(h, m, ncol, &lw);
+      if (lw > lwork) {
+        fail_w(MFS_ERR_CUDA, "SVD workspace larger than the one sized for the largest block");
+        break;
+      }
+      cusolverStatus_t sst = cusolverDnDgesvd(h, 'S', 'S', m, ncol, dB, m, dS, dU, m, dVT, ncol, dwork, lwork, drw, dinfo);
+      int hinfo = 0;
+      cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(hS.data(), dS, sizeof(double) * ncol, cudaMemcpyDeviceToHost, st);
+      cudaError_t es = cudaStreamSynchronize(st);
+      if (sst != CUSOLVER_STATUS_SUCCESS || es != cudaSuccess || hinfo != 0) {
+        fail_w(MFS_ERR_CUDA, "one-body SVD failed (cusolver status " + std::to_string((int)sst) + ", info " +
+                                 std::to_string(hinfo) + ")");
+        break;
+      }
+      // keep sigma >= eps * sigma_max (no assumption on the order the SVD returns them in)
+      double smax = 0;
+      for (int i = 0; i < ncol; ++i) smax = std::max(smax, hS[i]);
+      std::vector<int> keep;
+      for (int i = 0; i < ncol; ++i)
+        if (hS[i] >= p.eps_trunc * smax && hS[i] > 0) keep.push_back(i);
+      const int r = (int)keep.size();
+      if (r == 0) {
+        fail_w(MFS_ERR_NUMERIC, "one-body block has no singular value above the truncation level");
+        break;
+      }
+      if (cudaMemcpyAsync(dkeep, keep.data(), sizeof(int) * r, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        fail_w(MFS_ERR_CUDA, "upload of the retained singular indices failed");
+        break;
+      }
+      Factor F;
+      F.m = m;
+      F.ncol = ncol;
+      F.rank = r;
+      F.ldA = pad4(m);
+      F.ldV = pad4(r);
+      {
+        std::lock_guard<std::mutex> g(mtx);
+        F.A64 = c->dalloc<double>((size_t)r * F.ldA);
+        F.A32 = c->dalloc<float>((size_t)r * F.ldA);
+        F.V64 = c->dalloc<double>((size_t)ncol * F.ldV);
+        F.V32 = c->dalloc<float>((size_t)ncol * F.ldV);
+      }
+      if (!F.A64 || !F.A32 || !F.V64 || !F.V32) {
+        fail_w(MFS_ERR_OOM, "device allocation failed: one-body factors");
+        break;
+      }
+      pack_A_kernel<<<1024, 256, 0, st>>>(r, m, F.ldA, dU, dS, dkeep, F.A64, F.A32);
+      pack_V_kernel<<<1024, 256, 0, st>>>(ncol, r, F.ldV, dVT, dkeep, F.V64, F.V32);
+      cudaError_t el = cudaGetLastError();
+      if (el == cudaSuccess) el = cudaStreamSynchronize(st);  // keep and hS are reused next round
+      if (el != cudaSuccess) {
+        fail_w(MFS_ERR_CUDA, std::string("factor packing: ") + cudaGetErrorString(el));
+        break;
+      }
+      c->factors[f] = F;
+    }
+    cleanup();
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int w = 0; w < n_workers; ++w) pool.emplace_back(worker, w);
+    for (auto& t : pool) t.join();
+  }
+  if (wstat != MFS_OK) return c->fail(wstat, werr);
+
+  // ---- GEMV batches for step 1
+  std::vector<long long> tmp_off(P + 1, 0);
+  for (int k = 0; k < P; ++k) tmp_off[k + 1] = tmp_off[k] + c->factors[d.factor_id[k]].rank;
+  c->tmp_len = tmp_off[P];
+  {
+    std::vector<const double*> mA64(P), mV64(P);
+    std::vector<const float*> mA32(P), mV32(P);
+    std::vector<int> rA(P), cA(P), lA(P), rV(P), cV(P), lV(P);
+    std::vector<long long> xA(P), yA(P), xV(P), yV(P);
+    int maxA = 0, maxV = 0;
+    for (int k = 0; k < P; ++k) {
+      const Factor& F = c->factors[d.factor_id[k]];
+      mA64[k] = F.A64; mA32[k] = F.A32; mV64[k] = F.V64; mV32[k] = F.V32;
+      rA[k] = F.rank; cA[k] = F.m; lA[k] = F.ldA;
+      xA[k] = 3LL * d.colloc_off[k]; yA[k] = tmp_off[k];
+      rV[k] = F.ncol; cV[k] = F.rank; lV[k] = F.ldV;
+      xV[k] = tmp_off[k]; yV[k] = d.unk_off[k];
+      maxA = std::max(maxA, F.rank);
+      maxV = std::max(maxV, F.ncol);
+    }
+    const double** dm64 = nullptr;
+    const float** dm32 = nullptr;
+    if ((s = upload(c, dm64, mA64)) != MFS_OK) return s;
+    c->gA64.mat = dm64;
+    if ((s = upload(c, dm32, mA32)) != MFS_OK) return s;
+    c->gA32.mat = dm32;
+    if ((s = upload(c, dm64, mV64)) != MFS_OK) return s;
+    c->gV64.mat = dm64;
+    if ((s = upload(c, dm32, mV32)) != MFS_OK) return s;
+    c->gV32.mat = dm32;
+    int *d_rA, *d_cA, *d_lA, *d_rV, *d_cV, *d_lV;
+    long long *d_xA, *d_yA, *d_xV, *d_yV;
+    if ((s = upload(c, d_rA, rA)) || (s = upload(c, d_cA, cA)) || (s = upload(c, d_lA, lA)) || (s = upload(c, d_rV, rV)) ||
+        (s = upload(c, d_cV, cV)) || (s = upload(c, d_lV, lV)) || (s = upload(c, d_xA, xA)) || (s = upload(c, d_yA, yA)) ||
+        (s = upload(c, d_xV, xV)) || (s = upload(c, d_yV, yV)))
+      return s;
+    c->gA64.rows = c->gA32.rows = d_rA;
+    c->gA64.cols = c->gA32.cols = d_cA;
+    c->gA64.ld = c->gA32.ld = d_lA;
+    c->gA64.x_off = c->gA32.x_off = d_xA;
+    c->gA64.y_off = c->gA32.y_off = d_yA;
+    c->gA64.n_jobs = c->gA32.n_jobs = P;
+    c->gA64.max_rows = c->gA32.max_rows = maxA;
+    c->gV64.rows = c->gV32.rows = d_rV;
+    c->gV64.cols = c->gV32.cols = d_cV;
+    c->gV64.ld = c->gV32.ld = d_lV;
+    c->gV64.x_off = c->gV32.x_off = d_xV;
+    c->gV64.y_off = c->gV32.y_off = d_yV;
+    c->gV64.n_jobs = c->gV32.n_jobs = P;
+    c->gV64.max_rows = c->gV32.max_rows = maxV;
+  }
+
+  // ---- work vectors
+  const int n = c->n;
+  ALLOC_TRY(c, c->d_v, double, 3 * (size_t)P);
+  ALLOC_TRY(c, c->d_om, double, 3 * (size_t)P);
+  ALLOC_TRY(c, c->d_wb, double, n);
+  ALLOC_TRY(c, c->d_mu, double, n);
+  ALLOC_TRY(c, c->d_r, double, n);
+  ALLOC_TRY(c, c->d_w64, double, n);
+  ALLOC_TRY(c, c->d_tmp64, double, c->tmp_len);
+  ALLOC_TRY(c, c->d_lh64, double, c->n_unk);
+  ALLOC_TRY(c, c->d_lam, double, c->n_unk);
+  ALLOC_TRY(c, c->d_F, double, 3 * (size_t)P);
+  ALLOC_TRY(c, c->d_T, double, 3 * (size_t)P);
+  ALLOC_TRY(c, c->d_tmp32, float, c->tmp_len);
+  ALLOC_TRY(c, c->d_lh32, float, c->n_unk);
+  ALLOC_TRY(c, c->d_in32, float, std::max<long long>(n, c->n_unk));
+  ALLOC_TRY(c, c->d_out32, float, std::max<long long>(n, c->n_unk));
+  ALLOC_TRY(c, c->d_mu32, float, n);
+  c->nblk = std::max(1, std::min(1024, (n + 4095) / 4096));
+  ALLOC_TRY(c, c->d_partial, double, (size_t)c->nblk * 512);
+  ALLOC_TRY(c, c->d_h, double, 5 * 512);
+  CUDA_TRY(c, cudaMemsetAsync(c->d_v, 0, sizeof(double) * 3 * P, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_om, 0, sizeof(double) * 3 * P, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->state = 2;
+  c->solved = false;
+  c->have_bc = false;
+  return MFS_OK;
+}
+
+mfs_status mfs_sizes(const mfs_ctx* cc, mfs_sizes_t* out) {
+  mfs_ctx* c = const_cast<mfs_ctx*>(cc);
+  if (!c || !out) return MFS_ERR_ARG;
+  if (c->state < 2) return c->fail(MFS_ERR_STATE, "discretisation not built");
+  const HostDisc& d = c->hd;
+  out->P = d.P;
+  out->n_contacts = (int)d.contacts.size();
+  out->n_colloc = d.n_colloc();
+  out->n_proxy_total = d.P * d.prm.n_proxy;
+  out->n_image_nodes = d.n_img();
+  out->n_unknowns = (int)d.n_unknowns();
+  out->n_factors = (int)c->factors.size();
+  long long pairs = 0;
+  for (int k = 0; k < d.P; ++k) {
+    long long mk = d.colloc_off[k + 1] - d.colloc_off[k];
+    long long other = (long long)(d.P - 1) * d.prm.n_proxy + 3LL * (d.n_img() - (d.img_off[k + 1] - d.img_off[k]));
+    pairs += mk * other;
+  }
+  out->pairs_fp = pairs;
+  return MFS_OK;
+}
+
+mfs_status mfs_set_rigid_velocities(mfs_ctx* c, const double* v, const double* om) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!v || !om) return c->fail(MFS_ERR_ARG, "null velocity array");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_v, v, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_om, om, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->have_bc = true;
+  c->solved = false;
+  return MFS_OK;
+}
+
+mfs_status mfs_set_rigid_velocities_device(mfs_ctx* c, const double* v, const double* om) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!v || !om) return c->fail(MFS_ERR_ARG, "null velocity array");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_v, v, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_om, om, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  c->have_bc = true;
+  c->solved = false;
+  return MFS_OK;
+}
+
+mfs_status mfs_solve(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  mfs_solve_opts o;
+  if (opts) o = *opts; else mfs_default_solve_opts(&o);
+  if (o.restart < 1 || o.restart > 500 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 ||
+      (o.precision != MFS_FP64 && o.precision != MFS_MIXED && o.precision != MFS_FP32))
+    return c->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 500])");
+  const int n = c->n;
+  launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(), c->d_wb, c->stream);
+  CHECK_LAUNCH(c);
+  double bnorm = 0;
+  if ((s = norm64(c, c->d_wb, bnorm)) != MFS_OK) return s;
+  int iters = 0, refinements = 0;
+  double rel = 0;
+  bool converged = false;
+  if (!(bnorm > 0)) {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * n, c->stream));
+    converged = std::isfinite(bnorm);
+    if (!converged) return c->fail(MFS_ERR_NUMERIC, "boundary data is not finite");
+  } else if (o.precision == MFS_FP64 || o.precision == MFS_MIXED) {
+    // FP64 GMRES; MIXED evaluates the pair sums in double-float on the FP32 pipes.  The
+    // residual is re-evaluated with the same operator after each pass and the correction
+    // equation solved again if a restart-limited pass fell short (iterative refinement).
+    c->dw_pairs = (o.precision == MFS_MIXED);
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * n, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_r, c->d_wb, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    double rn = bnorm;
+    rel = 1.0;
+    for (int it = 0; it <= o.max_refine; ++it) {
+      if (rel <= o.tol) break;
+      if (it == o.max_refine || iters >= o.max_iter) break;
+      int it_in = 0;
+      double est = 0;
+      // solve G_hat e = r with the relative accuracy still missing, then mu += e
+      if ((s = gmres<double>(c, c->d_r, c->d_w64, std::min(0.5, 0.5 * o.tol / rel), o.restart, o.max_iter - iters,
+                             it_in, est)) != MFS_OK) {
+        c->dw_pairs = false;
+        return s;
+      }
+      iters += it_in;
+      {
+        double one = 1.0;
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_h + 4 * 512 + 8, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        launch_update<double>(n, 1, c->d_w64, n, c->d_h + 4 * 512 + 8, 1.0, c->d_mu, c->stream);
+      }
+      apply_op<double>(c, c->d_mu, c->d_w64);
+      launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
+      CHECK_LAUNCH(c);
+      double rprev = rn;
+      if ((s = norm64(c, c->d_r, rn)) != MFS_OK) {
+        c->dw_pairs = false;
+        return s;
+      }
+      rel = rn / bnorm;
+      if (it > 0) ++refinements;
+      if (!std::isfinite(rn)) {
+        c->dw_pairs = false;
+        return c->fail(MFS_ERR_NUMERIC, "residual is not finite");
+      }
+      if (rn > 0.9 * rprev && rel > o.tol) break;
+    }
+    c->dw_pairs = false;
+    converged = rel <= o.tol;
+  } else {
+    // MFS_FP32: FP64 residual, FP32 inner GMRES on the normalised residual
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * n, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_r, c->d_wb, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+    double rn = bnorm;
+    rel = 1.0;
+    for (int it = 0; it <= o.max_refine; ++it) {
+      if (rel <= o.tol) {
+        converged = true;
+        break;
+      }
+      if (it == o.max_refine || iters >= o.max_iter) break;
+      launch_convert<double, float>(n, c->d_r, 1.0 / rn, c->d_in32, c->stream);
+      int it_in = 0;
+      double est = 0;
+      if ((s = gmres<float>(c, c->d_in32, c->d_out32, std::max(o.inner_tol, o.tol / rel * 0.5), o.restart,
+                            o.max_iter - iters, it_in, est)) != MFS_OK)
+        return s;
+      iters += it_in;
+      launch_axpy_mixed(n, rn, c->d_out32, c->d_mu, c->stream);
+      apply_op<double>(c, c->d_mu, c->d_w64);
+      launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
+      CHECK_LAUNCH(c);
+      double rprev = rn;
+      if ((s = norm64(c, c->d_r, rn)) != MFS_OK) return s;
+      rel = rn / bnorm;
+      ++refinements;
+      if (!std::isfinite(rn)) return c->fail(MFS_ERR_NUMERIC, "refinement residual is not finite");
+      if (rn > 0.9 * rprev && rel > o.tol) break;  // refinement stagnates at the FP32 operator's accuracy
+    }
+    if (rel <= o.tol) converged = true;
+  }
+  // lambda = B^+ mu in FP64, then forces and torques
+  precond<double>(c, c->d_mu, c->d_lam);
+  launch_forces_torques(c->src, c->d_lam, c->d_F, c->d_T, c->stream);
+  CHECK_LAUNCH(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->solved = true;
+  if (info) {
+    info->iters = iters;
+    info->refinements = refinements;
+    info->rel_residual = rel;
+    info->converged = converged ? 1 : 0;
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (!converged) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "not converged: relative residual %.3e after %d iterations", rel, iters);
+    return c->fail(MFS_ERR_NOT_CONVERGED, buf);
+  }
+  return MFS_OK;
+}
+
+mfs_status mfs_get_forces_torques(mfs_ctx* c, double* F, double* T) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!c->solved) return c->fail(MFS_ERR_STATE, "no solution yet");
+  if (!F || !T) return c->fail(MFS_ERR_ARG, "null output");
+  CUDA_TRY(c, cudaMemcpyAsync(F, c->d_F, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(T, c->d_T, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
+mfs_status mfs_get_forces_torques_device(mfs_ctx* c, double* F, double* T) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!c->solved) return c->fail(MFS_ERR_STATE, "no solution yet");
+  if (!F || !T) return c->fail(MFS_ERR_ARG, "null output");
+  CUDA_TRY(c, cudaMemcpyAsync(F, c->d_F, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(T, c->d_T, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  return MFS_OK;
+}
+
+mfs_status mfs_eval_velocity(mfs_ctx* c, int npts, const double* x, double* u) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!c->solved) return c->fail(MFS_ERR_STATE, "no solution yet");
+  if (npts < 0 || (npts > 0 && (!x || !u))) return c->fail(MFS_ERR_ARG, "bad evaluation arrays");
+  if (npts == 0) return MFS_OK;
+  // temporary target set: absolute positions, no self exclusion (sphere index -1)
+  std::vector<double> t64(4 * (size_t)npts);
+  for (int i = 0; i < npts; ++i) {
+    for (int q = 0; q < 3; ++q) t64[4 * i + q] = x[3 * i + q];
+    t64[4 * i + 3] = 1.0;
+  }
+  int nt = (npts + kTileTargets - 1) / kTileTargets;
+  std::vector<int> ts(nt, -1), tst(nt), tcn(nt);
+  for (int t = 0; t < nt; ++t) {
+    tst[t] = t * kTileTargets;
+    tcn[t] = std::min(kTileTargets, npts - t * kTileTargets);
+  }
+  std::vector<void*> tmp;
+  auto ta = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    tmp.push_back(q);
+    return q;
+  };
+  auto done = [&](mfs_status st) {
+    cudaStreamSynchronize(c->stream);
+    for (void* q : tmp) cudaFree(q);
+    return st;
+  };
+  TargetSet tg;
+  tg.n = npts;
+  tg.n_tiles = nt;
+  tg.pos64 = (double*)ta(t64.size() * 8);
+  tg.tile_sphere = (int*)ta(nt * 4);
+  tg.tile_start = (int*)ta(nt * 4);
+  tg.tile_count = (int*)ta(nt * 4);
+  double* du = (double*)ta(3 * (size_t)npts * 8);
+  if (!tg.pos64 || !tg.tile_sphere || !tg.tile_start || !tg.tile_count || !du)
+    return done(c->fail(MFS_ERR_OOM, "device allocation failed: evaluation points"));
+  cudaMemcpyAsync(tg.pos64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(tg.tile_sphere, ts.data(), nt * 4, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(tg.tile_start, tst.data(), nt * 4, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(tg.tile_count, tcn.data(), nt * 4, cudaMemcpyHostToDevice, c->stream);
+  launch_pairs<double>(tg, c->src, c->d_lam, nullptr, du, c->hd.prm.visc, c->stream);
+  cudaMemcpyAsync(u, du, 3 * (size_t)npts * 8, cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return done(c->fail(MFS_ERR_CUDA, std::string("eval: ") + cudaGetErrorString(e)));
+  return done(MFS_OK);
+}
+
+mfs_status mfs_get_strengths(mfs_ctx* c, double* lambda, double* pos, int* type) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  const HostDisc& d = c->hd;
+  if (lambda) {
+    if (!c->solved) return c->fail(MFS_ERR_STATE, "no solution yet");
+    CUDA_TRY(c, cudaMemcpyAsync(lambda, c->d_lam, sizeof(double) * c->n_unk, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  if (pos || type) {
+    long long v = 0;
+    const int N = d.prm.n_proxy;
+    for (int k = 0; k < d.P; ++k) {
+      for (int j = 0; j < N; ++j, ++v) {
+        if (pos)
+          for (int q = 0; q < 3; ++q) pos[3 * v + q] = d.centres[3 * k + q] + d.proxy_rel[3 * j + q];
+        if (type) type[v] = 0;
+      }
+      for (int j = d.img_off[k]; j < d.img_off[k + 1]; ++j)
+        for (int t = 0; t < 3; ++t, ++v) {
+          if (pos)
+            for (int q = 0; q < 3; ++q) pos[3 * v + q] = d.image[3 * j + q];
+          if (type) type[v] = t;
+        }
+    }
+  }
+  return MFS_OK;
+}
+
+mfs_status mfs_get_collocation(mfs_ctx* c, double* x, double* w, int* owner) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  const HostDisc& d = c->hd;
+  if (x) std::copy(d.colloc.begin(), d.colloc.end(), x);
+  if (w) std::copy(d.weight.begin(), d.weight.end(), w);
+  if (owner) std::copy(d.owner.begin(), d.owner.end(), owner);
+  return MFS_OK;
+}
+
+mfs_status mfs_get_rhs(mfs_ctx* c, double* wb) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!wb) return c->fail(MFS_ERR_ARG, "null output");
+  launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(), c->d_wb, c->stream);
+  CHECK_LAUNCH(c);
+  CUDA_TRY(c, cudaMemcpyAsync(wb, c->d_wb, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
+// Runs one step of the operator on host data: stage inputs, compute, read back.
+static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* in1, const double* in2, double* out) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (precision != MFS_FP64 && precision != MFS_MIXED && precision != MFS_FP32)
+    return c->fail(MFS_ERR_ARG, "precision must be MFS_FP64, MFS_MIXED or MFS_FP32");
+  if (!in1 || !out || (which == 2 && !in2)) return c->fail(MFS_ERR_ARG, "null array");
+  const long long n = c->n, nu = c->n_unk;
+  const long long len1 = which == 2 ? nu : n;      // pairs: first input is lambda_hat
+  const long long lenout = which == 1 ? nu : n;    // precond: output in source space
+  double* d1 = which == 2 ? c->d_lam : c->d_mu;
+  // the operator-step entry points reuse the solution buffers; a later get_* must re-solve
+  c->solved = false;
+  CUDA_TRY(c, cudaMemcpyAsync(d1, in1, sizeof(double) * len1, cudaMemcpyHostToDevice, c->stream));
+  if (which == 2) CUDA_TRY(c, cudaMemcpyAsync(c->d_mu, in2, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+  double* dout = which == 1 ? c->d_lh64 : c->d_w64;
+  if (precision != MFS_FP32) {
+    c->dw_pairs = (precision == MFS_MIXED);
+    if (which == 0) apply_op<double>(c, c->d_mu, c->d_w64);
+    else if (which == 1) precond<double>(c, c->d_mu, c->d_lh64);
+    else if (c->dw_pairs) launch_pairs_dw(c->tg, c->src, c->d_lam, c->d_mu, c->d_w64, c->hd.prm.visc, c->stream);
+    else launch_pairs<double>(c->tg, c->src, c->d_lam, c->d_mu, c->d_w64, c->hd.prm.visc, c->stream);
+    c->dw_pairs = false;
+  } else {
+    launch_convert<double, float>(len1, d1, 1.0, c->d_in32, c->stream);
+    if (which == 0) {
+      apply_op<float>(c, c->d_in32, c->d_out32);
+    } else if (which == 1) {
+      precond<float>(c, c->d_in32, c->d_out32);
+    } else {
+      launch_convert<double, float>(n, c->d_mu, 1.0, c->d_mu32, c->stream);
+      launch_pairs<float>(c->tg, c->src, c->d_in32, c->d_mu32, c->d_out32, c->hd.prm.visc, c->stream);
+    }
+    launch_convert<float, double>(lenout, c->d_out32, 1.0, dout, c->stream);
+  }
+  CHECK_LAUNCH(c);
+  CUDA_TRY(c, cudaMemcpyAsync(out, dout, sizeof(double) * lenout, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
+mfs_status mfs_apply_operator(mfs_ctx* c, int precision, const double* mu, double* out) {
+  return run_step(c, precision, 0, mu, nullptr, out);
+}
+mfs_status mfs_apply_precond(mfs_ctx* c, int precision, const double* mu, double* lambda_hat) {
+  return run_step(c, precision, 1, mu, nullptr, lambda_hat);
+}
+mfs_status mfs_apply_pairs(mfs_ctx* c, int precision, const double* lambda_hat, const double* mu, double* out) {
+  return run_step(c, precision, 2, lambda_hat, mu, out);
+}
+
+}  // extern "C"

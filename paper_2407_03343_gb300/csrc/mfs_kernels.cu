@@ -1,0 +1,871 @@
+// CUDA kernels of the hot path (sm_103a).
+//
+//  pairs_kernel<T>     steps 2+3 of the G_hat apply (Sec. 2.2, eq. uAll): for every
+//                      collocation node x_i of sphere k,
+//                        out_i = mu_i + sqrt(w_i) sum_{k' != k} [S f + R t + D d](x_i - y)
+//                      over the proxy Stokeslets and the image S/R/D triples of all other
+//                      spheres (eq. lin_comb).  Direct summation, so the self block is
+//                      skipped instead of being added and subtracted (allowed by Sec. 2.2).
+//                      Sources are staged through shared memory in tiles; each thread owns
+//                      NT target nodes in registers; 1/|r| comes from rsqrt (FP32) or an
+//                      FP32 seed refined by Newton-Raphson (FP64).  FP32 sums run per tile
+//                      and are folded into Kahan-compensated accumulators across tiles.
+//                      Positions are stored relative to their sphere centre and shifted into
+//                      the target sphere's frame while staging, with the centre difference
+//                      taken in float-float, so near-contact distances keep FP32 accuracy.
+//  gemv_kernel<T>      batched row-major GEMV for the one-body pseudo-inverse factors
+//                      (eq. transform), HBM-bound.
+//  Krylov kernels      multi-dot, update, scale (GMRES with CGS2), FP64 partial sums.
+//  ft_kernel           forces and torques from the strengths (Sec. 2.3 remark), FP64.
+//  rhs_kernel          W u_bc (eq. bc, eq. lq2), FP64.
+//  assemble_self       B_k = W_k G^(kk) column-major FP64 for the one-time factorisation.
+#include <cmath>
+#include <cstdio>
+
+#include "mfs_internal.h"
+
+namespace mfs {
+namespace {
+
+constexpr int kPairThreads = 128;
+constexpr int kNT = 4;          // target nodes per thread
+constexpr int kTileProxy = 256; // proxy sources staged per round
+constexpr int kTileImg = 128;   // image nodes staged per round
+constexpr double kPi = 3.14159265358979323846;
+
+// four doubles moved as one 32-byte-aligned unit
+struct __align__(32) D4 {
+  double x, y, z, w;
+};
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+  using V4 = float4;
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ V4 mk(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+template <> struct Prec<double> {
+  using V4 = D4;
+  // 1/sqrt(x): FP32 hardware estimate refined by two Newton-Raphson steps
+  // y <- y (3 - x y^2) / 2, each of which roughly doubles the number of correct bits.
+  static __device__ __forceinline__ double rsq(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y;
+  }
+  static __device__ __forceinline__ V4 mk(double a, double b, double c, double d) { return D4{a, b, c, d}; }
+};
+
+// Kahan-compensated s += x.  FP64 accumulates directly.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+  float y = x - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+__device__ __forceinline__ void comp_add(double& s, double& c, double x) { (void)c; s += x; }
+
+// Centre of sphere o minus centre of the target frame, in the working precision.
+struct CentreShift32 {
+  const float* hi;
+  const float* lo;
+  float kh[3], kl[3];
+  __device__ void init(int k) {
+    for (int c = 0; c < 3; ++c) {
+      kh[c] = k >= 0 ? hi[3 * k + c] : 0.f;
+      kl[c] = k >= 0 ? lo[3 * k + c] : 0.f;
+    }
+  }
+  __device__ __forceinline__ float d(int o, int c) const { return (hi[3 * o + c] - kh[c]) + (lo[3 * o + c] - kl[c]); }
+};
+struct CentreShift64 {
+  const double* cen;
+  double kc[3];
+  __device__ void init(int k) {
+    for (int c = 0; c < 3; ++c) kc[c] = k >= 0 ? cen[3 * k + c] : 0.0;
+  }
+  __device__ __forceinline__ double d(int o, int c) const { return cen[3 * o + c] - kc[c]; }
+};
+template <typename T> struct ShiftOf;
+template <> struct ShiftOf<float> { using type = CentreShift32; };
+template <> struct ShiftOf<double> { using type = CentreShift64; };
+
+template <typename T>
+struct PairArgs {
+  const typename Prec<T>::V4* tgt;  // (x, y, z, sqrt w) relative to the tile's sphere (absolute if sphere < 0)
+  const int* tile_sphere;
+  const int* tile_start;
+  const int* tile_count;
+  const typename Prec<T>::V4* proxy;  // N, relative to the owner centre
+  int N, P;
+  const typename Prec<T>::V4* img;    // image nodes relative to the owner centre
+  const int* img_owner;
+  const int* img_off;
+  int n_img;
+  const long long* unk_off;
+  const float* cen_hi;
+  const float* cen_lo;
+  const double* cen64;
+  const T* lam;
+  const T* mu;   // may be null: then out = scale * sum (no W, no identity)
+  T* out;
+  T scale;       // 1 / (8 pi mu)
+  T dip;         // 2 mu: dipole strengths rescaled so that scale * dip = 1 / (4 pi)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
+  using V4 = typename Prec<T>::V4;
+  __shared__ V4 sp[kTileProxy];
+  __shared__ V4 sf[kTileProxy];
+  __shared__ V4 si[3 * kTileImg];
+
+  const int t = blockIdx.x;
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  typename ShiftOf<T>::type sh;
+  if constexpr (sizeof(T) == 4) { sh.hi = A.cen_hi; sh.lo = A.cen_lo; } else { sh.cen = A.cen64; }
+  sh.init(k);
+
+  T x[kNT], y[kNT], z[kNT], ux[kNT], uy[kNT], uz[kNT];
+  T sx[kNT], sy[kNT], sz[kNT], cx[kNT], cy[kNT], cz[kNT];
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    int node = start + (idx < cnt ? idx : cnt - 1);
+    V4 p = A.tgt[node];
+    x[q] = p.x; y[q] = p.y; z[q] = p.z;
+    ux[q] = uy[q] = uz[q] = T(0);
+    sx[q] = sy[q] = sz[q] = T(0);
+    cx[q] = cy[q] = cz[q] = T(0);
+  }
+  const T far = T(1e18);
+
+  // ---- proxy Stokeslets of every sphere but k
+  const int total = A.P * A.N;
+  for (int s0 = 0; s0 < total; s0 += kTileProxy) {
+    if (k >= 0 && s0 >= k * A.N && s0 + kTileProxy <= (k + 1) * A.N) continue;  // whole tile is self
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileProxy; i += kPairThreads) {
+      int j = s0 + i;
+      V4 pos = Prec<T>::mk(far, far, far, T(0)), str = Prec<T>::mk(T(0), T(0), T(0), T(0));
+      if (j < total) {
+        int o = j / A.N;
+        int jj = j - o * A.N;
+        V4 pr = A.proxy[jj];
+        pos = Prec<T>::mk(pr.x + sh.d(o, 0), pr.y + sh.d(o, 1), pr.z + sh.d(o, 2), T(0));
+        if (o != k) {
+          const T* l = A.lam + A.unk_off[o] + 3LL * jj;
+          str = Prec<T>::mk(l[0], l[1], l[2], T(0));
+        }
+      }
+      sp[i] = pos;
+      sf[i] = str;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < kTileProxy; ++j) {
+      const V4 p = sp[j];
+      const V4 f = sf[j];
+#pragma unroll
+      for (int q = 0; q < kNT; ++q) {
+        T dx = x[q] - p.x, dy = y[q] - p.y, dz = z[q] - p.z;
+        T r2 = dx * dx + dy * dy + dz * dz;
+        T ir = Prec<T>::rsq(r2);
+        T ir2 = ir * ir;
+        T rf = dx * f.x + dy * f.y + dz * f.z;
+        T c = rf * ir2;
+        ux[q] += ir * (f.x + c * dx);
+        uy[q] += ir * (f.y + c * dy);
+        uz[q] += ir * (f.z + c * dz);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kNT; ++q) {
+      comp_add(sx[q], cx[q], ux[q]);
+      comp_add(sy[q], cy[q], uy[q]);
+      comp_add(sz[q], cz[q], uz[q]);
+      ux[q] = uy[q] = uz[q] = T(0);
+    }
+  }
+
+  // ---- image nodes (Stokeslet + rotlet + potential dipole at one position)
+  const int self_lo = k >= 0 ? A.img_off[k] : 0, self_hi = k >= 0 ? A.img_off[k + 1] : 0;
+  for (int s0 = 0; s0 < A.n_img; s0 += kTileImg) {
+    if (k >= 0 && s0 >= self_lo && s0 + kTileImg <= self_hi) continue;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileImg; i += kPairThreads) {
+      int j = s0 + i;
+      V4 a = Prec<T>::mk(far, far, far, T(0)), b = Prec<T>::mk(T(0), T(0), T(0), T(0)), c = b;
+      if (j < A.n_img) {
+        int o = A.img_owner[j];
+        V4 pr = A.img[j];
+        T px = pr.x + sh.d(o, 0), py = pr.y + sh.d(o, 1), pz = pr.z + sh.d(o, 2);
+        if (o != k) {
+          const T* l = A.lam + A.unk_off[o] + 3LL * A.N + 9LL * (j - A.img_off[o]);
+          a = Prec<T>::mk(px, py, pz, l[0]);
+          b = Prec<T>::mk(l[1], l[2], l[3], l[4]);
+          c = Prec<T>::mk(l[5], A.dip * l[6], A.dip * l[7], A.dip * l[8]);
+        } else {
+          a = Prec<T>::mk(px, py, pz, T(0));
+        }
+      }
+      si[3 * i] = a;
+      si[3 * i + 1] = b;
+      si[3 * i + 2] = c;
+    }
+    __syncthreads();
+    for (int j = 0; j < kTileImg; ++j) {
+      const V4 a = si[3 * j], b = si[3 * j + 1], c = si[3 * j + 2];
+      // f = (a.w, b.x, b.y), t = (b.z, b.w, c.x), d = (c.y, c.z, c.w)
+#pragma unroll
+      for (int q = 0; q < kNT; ++q) {
+        T dx = x[q] - a.x, dy = y[q] - a.y, dz = z[q] - a.z;
+        T r2 = dx * dx + dy * dy + dz * dz;
+        T ir = Prec<T>::rsq(r2);
+        T ir2 = ir * ir;
+        T ir3 = ir * ir2;
+        // Stokeslet
+        T rf = dx * a.w + dy * b.x + dz * b.y;
+        T cs = rf * ir2;
+        T vx = ir * (a.w + cs * dx), vy = ir * (b.x + cs * dy), vz = ir * (b.y + cs * dz);
+        // rotlet: (t x r) / r^3
+        vx += ir3 * (b.w * dz - c.x * dy);
+        vy += ir3 * (c.x * dx - b.z * dz);
+        vz += ir3 * (b.z * dy - b.w * dx);
+        // potential dipole: -d / r^3 + 3 (d.r) r / r^5
+        T rd = dx * c.y + dy * c.z + dz * c.w;
+        T c3 = T(3) * rd * ir3 * ir2;
+        vx += c3 * dx - ir3 * c.y;
+        vy += c3 * dy - ir3 * c.z;
+        vz += c3 * dz - ir3 * c.w;
+        ux[q] += vx;
+        uy[q] += vy;
+        uz[q] += vz;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kNT; ++q) {
+      comp_add(sx[q], cx[q], ux[q]);
+      comp_add(sy[q], cy[q], uy[q]);
+      comp_add(sz[q], cz[q], uz[q]);
+      ux[q] = uy[q] = uz[q] = T(0);
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    if (idx < cnt) {
+      long long node = start + idx;
+      T sw = A.tgt[node].w;
+      T gx = (sx[q] + cx[q]) * A.scale, gy = (sy[q] + cy[q]) * A.scale, gz = (sz[q] + cz[q]) * A.scale;
+      if (A.mu) {
+        A.out[3 * node] = A.mu[3 * node] + sw * gx;
+        A.out[3 * node + 1] = A.mu[3 * node + 1] + sw * gy;
+        A.out[3 * node + 2] = A.mu[3 * node + 2] + sw * gz;
+      } else {
+        A.out[3 * node] = gx;
+        A.out[3 * node + 1] = gy;
+        A.out[3 * node + 2] = gz;
+      }
+    }
+  }
+}
+
+template <typename T>
+PairArgs<T> make_args(const TargetSet& tg, const SourceSet& src, const T* lam, const T* mu, T* out, double visc) {
+  PairArgs<T> A;
+  if constexpr (sizeof(T) == 4) {
+    A.tgt = tg.pos32;
+    A.proxy = src.proxy32;
+    A.img = src.img32;
+  } else {
+    A.tgt = reinterpret_cast<const D4*>(tg.pos64);
+    A.proxy = reinterpret_cast<const D4*>(src.proxy64);
+    A.img = reinterpret_cast<const D4*>(src.img64);
+  }
+  A.tile_sphere = tg.tile_sphere;
+  A.tile_start = tg.tile_start;
+  A.tile_count = tg.tile_count;
+  A.N = src.N;
+  A.P = src.P;
+  A.img_owner = src.img_owner;
+  A.img_off = src.img_off;
+  A.n_img = src.n_img;
+  A.unk_off = src.unk_off;
+  A.cen_hi = src.cen_hi;
+  A.cen_lo = src.cen_lo;
+  A.cen64 = src.cen64;
+  A.lam = lam;
+  A.mu = mu;
+  A.out = out;
+  A.scale = T(1.0 / (8.0 * kPi * visc));
+  A.dip = T(2.0 * visc);
+  return A;
+}
+
+// ------------------------------------------------------------------ double-float pair kernel
+// FP64-accurate pair sums on the FP32 pipes.  A value is an unevaluated sum hi + lo of two
+// floats (double-word arithmetic).  Error-free transforms: TwoSum (Knuth, TAOCP vol. 2),
+// FastTwoSum and TwoProd via FMA (Dekker 1971); DW+DW and DW*DW follow the "sloppy" sum
+// and the FMA-based product of Joldes, Muller and Popescu (ACM TOMS 44, 2017), whose
+// absolute errors stay at ~2^-46 of the operands even under cancellation, which is what
+// the pair sums need: the strengths lambda_hat = B^+ mu can exceed the field they produce
+// by 1e9 or more (Sec. 2.2, truncation 5e-12), so every term must be accurate to ~1e-14.
+struct dw {
+  float h, l;
+};
+// The _rn intrinsics are never contracted into FMAs, which the error-free transforms
+// rely on (a fused a*b + w would break the rounded product they assume).
+__device__ __forceinline__ dw two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dw fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ dw two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+  dw s = two_sum(x.h, y.h);
+  float v = __fadd_rn(x.l, y.l);
+  return fast_two_sum(s.h, __fadd_rn(s.l, v));
+}
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw{-y.h, -y.l}); }
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+  dw c = two_prod(x.h, y.h);
+  float t = __fmul_rn(x.h, y.l);
+  t = __fmaf_rn(x.l, y.h, t);
+  return fast_two_sum(c.h, __fadd_rn(c.l, t));
+}
+__device__ __forceinline__ dw dw_mul_f(dw x, float y) {
+  dw c = two_prod(x.h, y);
+  return fast_two_sum(c.h, __fmaf_rn(x.l, y, c.l));
+}
+__device__ __forceinline__ dw dw_split(double v) {
+  float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double dw_join(dw x) { return (double)x.h + (double)x.l; }
+// 1/sqrt(x): FP32 estimate, one FP32 Newton step, one double-word Newton step
+// y <- y + y (1 - x y^2) / 2.
+__device__ __forceinline__ dw dw_rsqrt(dw x) {
+  float s = rsqrtf(x.h);
+  s = __fmul_rn(s, __fmaf_rn(__fmul_rn(-0.5f, x.h), __fmul_rn(s, s), 1.5f));
+  dw s2 = two_prod(s, s);
+  dw e = dw_mul(x, s2);
+  float h = __fsub_rn(__fsub_rn(1.0f, e.h), e.l);
+  return fast_two_sum(s, __fmul_rn(__fmul_rn(0.5f, s), h));
+}
+
+struct __align__(16) DWPos {
+  float xh, yh, zh, pad0;
+  float xl, yl, zl, pad1;
+};
+
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A) {
+  __shared__ float4 sp[2 * kTileProxy];   // position hi, lo
+  __shared__ float4 sf[2 * kTileProxy];   // strength hi, lo
+  __shared__ float4 si[6 * kTileImg];     // image node: 12 hi values (3 float4), then 12 lo values (3 float4)
+
+  const int t = blockIdx.x;
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift64 sh;
+  sh.cen = A.cen64;
+  sh.init(k);
+
+  dw x[kNT], y[kNT], z[kNT], ux[kNT], uy[kNT], uz[kNT];
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    int node = start + (idx < cnt ? idx : cnt - 1);
+    D4 p = A.tgt[node];
+    x[q] = dw_split(p.x);
+    y[q] = dw_split(p.y);
+    z[q] = dw_split(p.z);
+    ux[q] = uy[q] = uz[q] = dw{0.f, 0.f};
+  }
+  const double far = 1e18;
+
+  const int total = A.P * A.N;
+  for (int s0 = 0; s0 < total; s0 += kTileProxy) {
+    if (k >= 0 && s0 >= k * A.N && s0 + kTileProxy <= (k + 1) * A.N) continue;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileProxy; i += kPairThreads) {
+      int j = s0 + i;
+      double px = far, py = far, pz = far, fx = 0, fy = 0, fz = 0;
+      if (j < total) {
+        int o = j / A.N;
+        int jj = j - o * A.N;
+        D4 pr = A.proxy[jj];
+        px = pr.x + sh.d(o, 0);
+        py = pr.y + sh.d(o, 1);
+        pz = pr.z + sh.d(o, 2);
+        if (o != k) {
+          const double* l = A.lam + A.unk_off[o] + 3LL * jj;
+          fx = l[0]; fy = l[1]; fz = l[2];
+        }
+      }
+      dw a = dw_split(px), b = dw_split(py), c = dw_split(pz);
+      sp[2 * i] = make_float4(a.h, b.h, c.h, 0.f);
+      sp[2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
+      a = dw_split(fx); b = dw_split(fy); c = dw_split(fz);
+      sf[2 * i] = make_float4(a.h, b.h, c.h, 0.f);
+      sf[2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
+    }
+    __syncthreads();
+    for (int j = 0; j < kTileProxy; ++j) {
+      const float4 ph = sp[2 * j], pl = sp[2 * j + 1];
+      const float4 fh = sf[2 * j], fl = sf[2 * j + 1];
+      const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
+#pragma unroll
+      for (int q = 0; q < kNT; ++q) {
+        dw dx = dw_sub(x[q], dw{ph.x, pl.x});
+        dw dy = dw_sub(y[q], dw{ph.y, pl.y});
+        dw dz = dw_sub(z[q], dw{ph.z, pl.z});
+        dw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
+        dw ir = dw_rsqrt(r2);
+        dw ir2 = dw_mul(ir, ir);
+        dw rf = dw_add(dw_add(dw_mul(dx, fx), dw_mul(dy, fy)), dw_mul(dz, fz));
+        dw c = dw_mul(rf, ir2);
+        ux[q] = dw_add(ux[q], dw_mul(ir, dw_add(fx, dw_mul(c, dx))));
+        uy[q] = dw_add(uy[q], dw_mul(ir, dw_add(fy, dw_mul(c, dy))));
+        uz[q] = dw_add(uz[q], dw_mul(ir, dw_add(fz, dw_mul(c, dz))));
+      }
+    }
+  }
+
+  const int self_lo = k >= 0 ? A.img_off[k] : 0, self_hi = k >= 0 ? A.img_off[k + 1] : 0;
+  for (int s0 = 0; s0 < A.n_img; s0 += kTileImg) {
+    if (k >= 0 && s0 >= self_lo && s0 + kTileImg <= self_hi) continue;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileImg; i += kPairThreads) {
+      int j = s0 + i;
+      double v[12] = {far, far, far, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      if (j < A.n_img) {
+        int o = A.img_owner[j];
+        D4 pr = A.img[j];
+        v[0] = pr.x + sh.d(o, 0);
+        v[1] = pr.y + sh.d(o, 1);
+        v[2] = pr.z + sh.d(o, 2);
+        if (o != k) {
+          const double* l = A.lam + A.unk_off[o] + 3LL * A.N + 9LL * (j - A.img_off[o]);
+          for (int q = 0; q < 6; ++q) v[3 + q] = l[q];
+          for (int q = 6; q < 9; ++q) v[3 + q] = A.dip * l[q];
+        }
+      }
+      // node i occupies si[6i .. 6i+5]: hi of (x, y, z, f, t, d) then lo of the same 12 values
+      float hv[12], lv[12];
+      for (int q = 0; q < 12; ++q) {
+        dw s = dw_split(v[q]);
+        hv[q] = s.h;
+        lv[q] = s.l;
+      }
+      si[6 * i] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      si[6 * i + 1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+      si[6 * i + 2] = make_float4(hv[8], hv[9], hv[10], hv[11]);
+      si[6 * i + 3] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      si[6 * i + 4] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+      si[6 * i + 5] = make_float4(lv[8], lv[9], lv[10], lv[11]);
+    }
+    __syncthreads();
+    for (int j = 0; j < kTileImg; ++j) {
+      const float4 h0 = si[6 * j], h1 = si[6 * j + 1], h2 = si[6 * j + 2];
+      const float4 l0 = si[6 * j + 3], l1 = si[6 * j + 4], l2 = si[6 * j + 5];
+      const dw px{h0.x, l0.x}, py{h0.y, l0.y}, pz{h0.z, l0.z};
+      const dw fx{h0.w, l0.w}, fy{h1.x, l1.x}, fz{h1.y, l1.y};
+      const dw tx{h1.z, l1.z}, ty{h1.w, l1.w}, tz{h2.x, l2.x};
+      const dw qx{h2.y, l2.y}, qy{h2.z, l2.z}, qz{h2.w, l2.w};
+#pragma unroll
+      for (int q = 0; q < kNT; ++q) {
+        dw dx = dw_sub(x[q], px), dy = dw_sub(y[q], py), dz = dw_sub(z[q], pz);
+        dw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
+        dw ir = dw_rsqrt(r2);
+        dw ir2 = dw_mul(ir, ir);
+        dw ir3 = dw_mul(ir, ir2);
+        // Stokeslet
+        dw rf = dw_add(dw_add(dw_mul(dx, fx), dw_mul(dy, fy)), dw_mul(dz, fz));
+        dw cs = dw_mul(rf, ir2);
+        dw vx = dw_mul(ir, dw_add(fx, dw_mul(cs, dx)));
+        dw vy = dw_mul(ir, dw_add(fy, dw_mul(cs, dy)));
+        dw vz = dw_mul(ir, dw_add(fz, dw_mul(cs, dz)));
+        // rotlet (t x r) / r^3
+        vx = dw_add(vx, dw_mul(ir3, dw_sub(dw_mul(ty, dz), dw_mul(tz, dy))));
+        vy = dw_add(vy, dw_mul(ir3, dw_sub(dw_mul(tz, dx), dw_mul(tx, dz))));
+        vz = dw_add(vz, dw_mul(ir3, dw_sub(dw_mul(tx, dy), dw_mul(ty, dx))));
+        // potential dipole -d / r^3 + 3 (d.r) r / r^5
+        dw rd = dw_add(dw_add(dw_mul(dx, qx), dw_mul(dy, qy)), dw_mul(dz, qz));
+        dw c3 = dw_mul(dw_mul(rd, ir3), ir2);
+        c3 = dw_mul_f(c3, 3.0f);
+        vx = dw_add(vx, dw_sub(dw_mul(c3, dx), dw_mul(ir3, qx)));
+        vy = dw_add(vy, dw_sub(dw_mul(c3, dy), dw_mul(ir3, qy)));
+        vz = dw_add(vz, dw_sub(dw_mul(c3, dz), dw_mul(ir3, qz)));
+        ux[q] = dw_add(ux[q], vx);
+        uy[q] = dw_add(uy[q], vy);
+        uz[q] = dw_add(uz[q], vz);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int q = 0; q < kNT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    if (idx < cnt) {
+      long long node = start + idx;
+      double sw = A.tgt[node].w;
+      double gx = dw_join(ux[q]) * A.scale, gy = dw_join(uy[q]) * A.scale, gz = dw_join(uz[q]) * A.scale;
+      if (A.mu) {
+        A.out[3 * node] = A.mu[3 * node] + sw * gx;
+        A.out[3 * node + 1] = A.mu[3 * node + 1] + sw * gy;
+        A.out[3 * node + 2] = A.mu[3 * node + 2] + sw * gz;
+      } else {
+        A.out[3 * node] = gx;
+        A.out[3 * node + 1] = gy;
+        A.out[3 * node + 2] = gz;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ batched GEMV
+constexpr int kGemvThreads = 256;
+constexpr int kGemvRowsPerWarp = 2;
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int w = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int w = 2; };
+
+template <typename T>
+__device__ __forceinline__ T dot_vec(const typename Vec<T>::type& m, const T* x);
+template <> __device__ __forceinline__ float dot_vec<float>(const float4& m, const float* x) {
+  return m.x * __ldg(x) + m.y * __ldg(x + 1) + m.z * __ldg(x + 2) + m.w * __ldg(x + 3);
+}
+template <> __device__ __forceinline__ double dot_vec<double>(const double2& m, const double* x) {
+  return m.x * __ldg(x) + m.y * __ldg(x + 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, const T* __restrict__ x, T* __restrict__ y) {
+  using VT = typename Vec<T>::type;
+  constexpr int W = Vec<T>::w;
+  const int job = blockIdx.y;
+  const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = (blockIdx.x * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
+  if (r0 >= nr) return;
+  const T* M = B.mat[job];
+  const T* xv = x + B.x_off[job];
+  T acc[kGemvRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) acc[r] = T(0);
+  const int nvec = nc / W;
+  for (int v = lane; v < nvec; v += 32) {
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) {
+        VT m = reinterpret_cast<const VT*>(M + (long long)row * ld)[v];
+        acc[r] += dot_vec<T>(m, xv + v * W);
+      }
+    }
+  }
+  for (int c = nvec * W + lane; c < nc; c += 32) {
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) acc[r] += M[(long long)row * ld + c] * xv[c];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+    T s = acc[r];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && r0 + r < nr) y[B.y_off[job] + r0 + r] = s;
+  }
+}
+
+// ------------------------------------------------------------------ Krylov helpers
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__global__ void multidot_kernel(int n, const T* __restrict__ V, long long ldv, const T* __restrict__ w,
+                                double* __restrict__ partial, int nblk) {
+  const int b = blockIdx.x, i = blockIdx.y;
+  const int chunk = (n + nblk - 1) / nblk;
+  const int lo = b * chunk, hi = min(n, lo + chunk);
+  const T* v = V + (long long)i * ldv;
+  T s = T(0);
+  for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) s += v[e] * w[e];
+  double d = (double)s;
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  __shared__ double red[kRedThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    partial[(long long)i * nblk + b] = t;
+  }
+}
+
+__global__ void reduce_partials_kernel(int nvec, int nblk, const double* __restrict__ partial, double* __restrict__ h) {
+  const int i = blockIdx.x;
+  double s = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(long long)i * nblk + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    h[i] = t;
+  }
+}
+
+template <typename T>
+__global__ void update_kernel(int n, int nvec, const T* __restrict__ V, long long ldv, const double* __restrict__ h,
+                              double sign, T* __restrict__ w) {
+  __shared__ T hs[512];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = T(sign * h[i]);
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    T acc = w[e];
+    for (int i = 0; i < nvec; ++i) acc += hs[i] * V[(long long)i * ldv + e];
+    w[e] = acc;
+  }
+}
+
+template <typename T>
+__global__ void scale_copy_kernel(int n, const T* __restrict__ w, double s, T* __restrict__ out) {
+  T ss = T(s);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = ss * w[e];
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(long long n, const Tin* __restrict__ in, double s, Tout* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (Tout)(s * (double)in[e]);
+}
+
+__global__ void axpy_mixed_kernel(int n, double a, const float* __restrict__ x, double* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] += a * (double)x[e];
+}
+
+__global__ void sub_kernel(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = a[e] - b[e];
+}
+
+// ------------------------------------------------------------------ forces / torques
+__global__ void ft_kernel(int N, const double* __restrict__ proxy64, const double* __restrict__ img64,
+                          const int* __restrict__ img_off, const long long* __restrict__ unk_off,
+                          const double* __restrict__ lam, double* __restrict__ F, double* __restrict__ Tq) {
+  const int k = blockIdx.x;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double* l = lam + unk_off[k];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double* y = proxy64 + 4LL * j;
+    double fx = l[3 * j], fy = l[3 * j + 1], fz = l[3 * j + 2];
+    acc[0] += fx; acc[1] += fy; acc[2] += fz;
+    acc[3] += y[1] * fz - y[2] * fy;
+    acc[4] += y[2] * fx - y[0] * fz;
+    acc[5] += y[0] * fy - y[1] * fx;
+  }
+  const int i0 = img_off[k], i1 = img_off[k + 1];
+  for (int j = i0 + threadIdx.x; j < i1; j += blockDim.x) {
+    const double* y = img64 + 4LL * j;
+    const double* s = l + 3LL * N + 9LL * (j - i0);
+    double fx = s[0], fy = s[1], fz = s[2];
+    acc[0] += fx; acc[1] += fy; acc[2] += fz;
+    acc[3] += s[3] + y[1] * fz - y[2] * fy;
+    acc[4] += s[4] + y[2] * fx - y[0] * fz;
+    acc[5] += s[5] + y[0] * fy - y[1] * fx;
+  }
+  __shared__ double red[6][32];
+  for (int c = 0; c < 6; ++c) {
+    double s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double s = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    if (threadIdx.x < 3) F[3 * k + threadIdx.x] = s; else Tq[3 * k + threadIdx.x - 3] = s;
+  }
+}
+
+struct Bg { double v[15]; };
+
+__global__ void rhs_kernel(int n, const double* __restrict__ xabs, const int* __restrict__ owner,
+                           const double* __restrict__ sqrtw, const double* __restrict__ cen,
+                           const double* __restrict__ v, const double* __restrict__ om, Bg bg, double* __restrict__ wb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int o = owner[i];
+    double x0 = xabs[3 * i], x1 = xabs[3 * i + 1], x2 = xabs[3 * i + 2];
+    double r0 = x0 - cen[3 * o], r1 = x1 - cen[3 * o + 1], r2 = x2 - cen[3 * o + 2];
+    const double* w = om + 3 * o;
+    double u0 = v[3 * o] + w[1] * r2 - w[2] * r1;
+    double u1 = v[3 * o + 1] + w[2] * r0 - w[0] * r2;
+    double u2 = v[3 * o + 2] + w[0] * r1 - w[1] * r0;
+    // background u_inf = U + E x + Omega x x, subtracted (eq. bc)
+    const double* E = bg.v + 3;
+    const double* Om = bg.v + 12;
+    u0 -= bg.v[0] + E[0] * x0 + E[1] * x1 + E[2] * x2 + Om[1] * x2 - Om[2] * x1;
+    u1 -= bg.v[1] + E[3] * x0 + E[4] * x1 + E[5] * x2 + Om[2] * x0 - Om[0] * x2;
+    u2 -= bg.v[2] + E[6] * x0 + E[7] * x1 + E[8] * x2 + Om[0] * x1 - Om[1] * x0;
+    double s = sqrtw[i];
+    wb[3 * i] = s * u0;
+    wb[3 * i + 1] = s * u1;
+    wb[3 * i + 2] = s * u2;
+  }
+}
+
+// B[(3 s + c) lda + 3 i + r] = sqrt(w_i) K_type(x_i - y_s)[r][c]
+__global__ void assemble_self_kernel(int m, int n_src, const double* __restrict__ xrel, const double* __restrict__ sqrtw,
+                                     const double* __restrict__ yrel, const int* __restrict__ type, double scale,
+                                     double* __restrict__ B, long long lda) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= (long long)m * n_src) return;
+  int i = (int)(id % m);
+  int s = (int)(id / m);
+  double r[3] = {xrel[3 * i] - yrel[3 * s], xrel[3 * i + 1] - yrel[3 * s + 1], xrel[3 * i + 2] - yrel[3 * s + 2]};
+  double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double ir = 1.0 / sqrt(r2);
+  double ir3 = ir * ir * ir;
+  double K[3][3];
+  int ty = type[s];
+  if (ty == 0) {
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) K[a][b] = scale * ((a == b ? ir : 0.0) + r[a] * r[b] * ir3);
+  } else if (ty == 1) {
+    double c = scale * ir3;
+    K[0][0] = 0; K[0][1] = c * r[2]; K[0][2] = -c * r[1];
+    K[1][0] = -c * r[2]; K[1][1] = 0; K[1][2] = c * r[0];
+    K[2][0] = c * r[1]; K[2][1] = -c * r[0]; K[2][2] = 0;
+  } else {
+    double c = 1.0 / (4.0 * kPi);
+    double ir5 = ir3 * ir * ir;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) K[a][b] = c * ((a == b ? -ir3 : 0.0) + 3.0 * r[a] * r[b] * ir5);
+  }
+  double w = sqrtw[i];
+  for (int c = 0; c < 3; ++c)
+    for (int rr = 0; rr < 3; ++rr) B[(3LL * s + c) * lda + 3LL * i + rr] = w * K[rr][c];
+}
+
+inline int grid_for(long long n, int threads, int cap = 152 * 16) {
+  long long g = (n + threads - 1) / threads;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu, T* out, double visc,
+                  cudaStream_t st) {
+  if (tg.n_tiles == 0) return;
+  PairArgs<T> A = make_args<T>(tg, src, lam_hat, mu, out, visc);
+  pairs_kernel<T><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+}
+template void launch_pairs<float>(const TargetSet&, const SourceSet&, const float*, const float*, float*, double, cudaStream_t);
+template void launch_pairs<double>(const TargetSet&, const SourceSet&, const double*, const double*, double*, double, cudaStream_t);
+
+void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu, double* out,
+                     double visc, cudaStream_t st) {
+  if (tg.n_tiles == 0) return;
+  PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc);
+  pairs_dw_kernel<<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+}
+
+template <typename T>
+void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st) {
+  if (b.n_jobs == 0 || b.max_rows == 0) return;
+  const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
+  dim3 grid((b.max_rows + rows_per_cta - 1) / rows_per_cta, b.n_jobs);
+  gemv_kernel<T><<<grid, kGemvThreads, 0, st>>>(b, x, y);
+}
+template void launch_gemv<float>(const GemvBatch<float>&, const float*, float*, cudaStream_t);
+template void launch_gemv<double>(const GemvBatch<double>&, const double*, double*, cudaStream_t);
+
+template <typename T>
+void launch_multidot(int n, int nvec, const T* V, long long ldv, const T* w, double* partial, int nblk, cudaStream_t st) {
+  dim3 grid(nblk, nvec);
+  multidot_kernel<T><<<grid, kRedThreads, 0, st>>>(n, V, ldv, w, partial, nblk);
+}
+template void launch_multidot<float>(int, int, const float*, long long, const float*, double*, int, cudaStream_t);
+template void launch_multidot<double>(int, int, const double*, long long, const double*, double*, int, cudaStream_t);
+
+void launch_reduce_partials(int nvec, int nblk, const double* partial, double* h, cudaStream_t st) {
+  reduce_partials_kernel<<<nvec, 256, 0, st>>>(nvec, nblk, partial, h);
+}
+
+template <typename T>
+void launch_update(int n, int nvec, const T* V, long long ldv, const double* h, double sign, T* w, cudaStream_t st) {
+  update_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(n, nvec, V, ldv, h, sign, w);
+}
+template void launch_update<float>(int, int, const float*, long long, const double*, double, float*, cudaStream_t);
+template void launch_update<double>(int, int, const double*, long long, const double*, double, double*, cudaStream_t);
+
+template <typename T>
+void launch_scale_copy(int n, const T* w, double s, T* out, cudaStream_t st) {
+  scale_copy_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(n, w, s, out);
+}
+template void launch_scale_copy<float>(int, const float*, double, float*, cudaStream_t);
+template void launch_scale_copy<double>(int, const double*, double, double*, cudaStream_t);
+
+template <typename Tin, typename Tout>
+void launch_convert(long long n, const Tin* in, double s, Tout* out, cudaStream_t st) {
+  convert_kernel<Tin, Tout><<<grid_for(n, 256), 256, 0, st>>>(n, in, s, out);
+}
+template void launch_convert<double, float>(long long, const double*, double, float*, cudaStream_t);
+template void launch_convert<float, double>(long long, const float*, double, double*, cudaStream_t);
+template void launch_convert<double, double>(long long, const double*, double, double*, cudaStream_t);
+
+void launch_axpy_mixed(int n, double a, const float* x, double* y, cudaStream_t st) {
+  axpy_mixed_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, x, y);
+}
+void launch_sub(int n, const double* a, const double* b, double* out, cudaStream_t st) {
+  sub_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, b, out);
+}
+
+void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st) {
+  ft_kernel<<<src.P, 256, 0, st>>>(src.N, src.proxy64, src.img64, src.img_off, src.unk_off, lam, F, T);
+}
+
+void launch_rhs(int n, const double* colloc_abs, const int* owner, const double* sqrtw, const double* cen,
+                const double* v, const double* om, const double* bg, double* wb, cudaStream_t st) {
+  Bg b;
+  for (int i = 0; i < 15; ++i) b.v[i] = bg[i];
+  rhs_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, colloc_abs, owner, sqrtw, cen, v, om, b, wb);
+}
+
+void launch_assemble_self(const HostDisc& hd, int k, const double* d_colloc_rel, const double* d_sqrtw,
+                          const double* d_src_rel, const int* d_src_type, int n_src, double* B, int lda,
+                          cudaStream_t st) {
+  int m = hd.colloc_off[k + 1] - hd.colloc_off[k];
+  long long tot = (long long)m * n_src;
+  int threads = 256;
+  long long blocks = (tot + threads - 1) / threads;
+  assemble_self_kernel<<<(unsigned)blocks, threads, 0, st>>>(m, n_src, d_colloc_rel, d_sqrtw, d_src_rel, d_src_type,
+                                                             1.0 / (8.0 * kPi * hd.prm.visc), B, lda);
+}
+
+}  // namespace mfs

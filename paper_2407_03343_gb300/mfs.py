@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libmfs (include/mfs.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays to
+pointers, checks status codes and raises ``MfsError`` on failure.  If libmfs.so has not
+been built, importing the library raises immediately -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmfs.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "mfs.h")
+
+FP64 = 0
+MIXED = 1
+FP32 = 2
+
+STATUS = {0: "MFS_OK", -1: "MFS_ERR_ARG", -2: "MFS_ERR_GEOMETRY", -3: "MFS_ERR_UNSUPPORTED",
+          -4: "MFS_ERR_STATE", -5: "MFS_ERR_NOT_CONVERGED", -6: "MFS_ERR_NUMERIC", -7: "MFS_ERR_OOM",
+          -8: "MFS_ERR_CUDA", -9: "MFS_ERR_TIMEOUT"}
+
+
+class Params(C.Structure):
+    _fields_ = [("n_proxy", C.c_int), ("r_proxy", C.c_double), ("m_basic", C.c_int),
+                ("delta_offset", C.c_double), ("alpha1", C.c_int), ("alpha2", C.c_int),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps_trunc", C.c_double),
+                ("nim_a", C.c_double), ("nim_b", C.c_double), ("nim_cut", C.c_double),
+                ("nim_max", C.c_int), ("nim_fixed", C.c_int), ("left_precond", C.c_int),
+                ("visc", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("restart", C.c_int), ("max_refine", C.c_int), ("inner_tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("rel_residual", C.c_double),
+                ("seconds", C.c_double), ("converged", C.c_int)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [("P", C.c_int), ("n_contacts", C.c_int), ("n_colloc", C.c_int),
+                ("n_proxy_total", C.c_int), ("n_image_nodes", C.c_int), ("n_unknowns", C.c_int),
+                ("n_factors", C.c_int), ("pairs_fp", C.c_longlong)]
+
+
+class MfsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+
+
+def lib():
+    """Load libmfs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sig = {
+        "mfs_default_params": (None, [C.POINTER(Params)]),
+        "mfs_default_solve_opts": (None, [C.POINTER(SolveOpts)]),
+        "mfs_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
+        "mfs_destroy": (None, [P]),
+        "mfs_last_error": (C.c_char_p, [P]),
+        "mfs_set_spheres": (C.c_int, [P, C.c_int, _D, _D]),
+        "mfs_set_rigid_velocities": (C.c_int, [P, _D, _D]),
+        "mfs_set_rigid_velocities_device": (C.c_int, [P, P, P]),
+        "mfs_set_background_flow": (C.c_int, [P, _D, _D, _D]),
+        "mfs_build": (C.c_int, [P, C.POINTER(Params)]),
+        "mfs_sizes": (C.c_int, [P, C.POINTER(Sizes)]),
+        "mfs_solve": (C.c_int, [P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "mfs_get_forces_torques": (C.c_int, [P, _D, _D]),
+        "mfs_get_forces_torques_device": (C.c_int, [P, P, P]),
+        "mfs_eval_velocity": (C.c_int, [P, C.c_int, _D, _D]),
+        "mfs_get_strengths": (C.c_int, [P, _D, _D, _I]),
+        "mfs_get_collocation": (C.c_int, [P, _D, _D, _I]),
+        "mfs_get_rhs": (C.c_int, [P, _D]),
+        "mfs_apply_operator": (C.c_int, [P, C.c_int, _D, _D]),
+        "mfs_apply_precond": (C.c_int, [P, C.c_int, _D, _D]),
+        "mfs_apply_pairs": (C.c_int, [P, C.c_int, _D, _D, _D]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_functions():
+    """Names of the functions include/mfs.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mfs_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(_I) if a is not None else None
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().mfs_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def default_solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().mfs_default_solve_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One solver context on one GPU (mirrors mfs_create ... mfs_destroy)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._L = lib()
+        self._h = C.c_void_p()
+        st = self._L.mfs_create(C.byref(self._h), int(device), C.c_void_p(stream) if stream else None)
+        if st != 0:
+            raise MfsError(st, "mfs_create failed")
+        self.P = 0
+
+    def close(self):
+        if self._h:
+            self._L.mfs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st, allow=()):
+        if st != 0 and st not in allow:
+            raise MfsError(st, self._L.mfs_last_error(self._h).decode())
+        return st
+
+    # -- problem set-up
+    def set_spheres(self, centres, radius=1.0):
+        c = _f64(centres).reshape(-1, 3)
+        P = c.shape[0]
+        r = _f64(np.broadcast_to(np.asarray(radius, dtype=np.float64), (P,)).copy())
+        self._check(self._L.mfs_set_spheres(self._h, P, _dp(c), _dp(r)))
+        self.P = P
+
+    def build(self, params: Params | None = None, **kw):
+        p = params if params is not None else default_params(**kw)
+        self._check(self._L.mfs_build(self._h, C.byref(p)))
+
+    def sizes(self) -> Sizes:
+        s = Sizes()
+        self._check(self._L.mfs_sizes(self._h, C.byref(s)))
+        return s
+
+    def set_rigid_velocities(self, v, omega):
+        v = _f64(v, (self.P, 3))
+        w = _f64(omega, (self.P, 3))
+        self._check(self._L.mfs_set_rigid_velocities(self._h, _dp(v), _dp(w)))
+
+    def set_rigid_velocities_device(self, v_ptr: int, omega_ptr: int):
+        self._check(self._L.mfs_set_rigid_velocities_device(self._h, C.c_void_p(v_ptr), C.c_void_p(omega_ptr)))
+
+    def set_background_flow(self, U=None, E=None, Omega=None):
+        a = _f64(U, (3,)) if U is not None else None
+        b = _f64(E, (3, 3)) if E is not None else None
+        c = _f64(Omega, (3,)) if Omega is not None else None
+        self._check(self._L.mfs_set_background_flow(self._h, _dp(a), _dp(b), _dp(c)))
+
+    # -- solve and outputs
+    def solve(self, opts: SolveOpts | None = None, allow_not_converged=False, **kw) -> SolveInfo:
+        o = opts if opts is not None else default_solve_opts(**kw)
+        info = SolveInfo()
+        allow = (-5,) if allow_not_converged else ()
+        self._check(self._L.mfs_solve(self._h, C.byref(o), C.byref(info)), allow)
+        return info
+
+    def forces_torques(self):
+        F = np.zeros((self.P, 3))
+        T = np.zeros((self.P, 3))
+        self._check(self._L.mfs_get_forces_torques(self._h, _dp(F), _dp(T)))
+        return F, T
+
+    def forces_torques_device(self, F_ptr: int, T_ptr: int):
+        self._check(self._L.mfs_get_forces_torques_device(self._h, C.c_void_p(F_ptr), C.c_void_p(T_ptr)))
+
+    def eval_velocity(self, x):
+        x = _f64(x).reshape(-1, 3)
+        u = np.zeros_like(x)
+        self._check(self._L.mfs_eval_velocity(self._h, x.shape[0], _dp(x), _dp(u)))
+        return u
+
+    def strengths(self, with_positions=False):
+        s = self.sizes()
+        lam = np.zeros(s.n_unknowns)
+        nv = s.n_unknowns // 3
+        pos = np.zeros((nv, 3)) if with_positions else None
+        typ = np.zeros(nv, dtype=np.int32) if with_positions else None
+        self._check(self._L.mfs_get_strengths(self._h, _dp(lam), _dp(pos), _ip(typ)))
+        return (lam, pos, typ) if with_positions else lam
+
+    def source_layout(self):
+        s = self.sizes()
+        nv = s.n_unknowns // 3
+        pos = np.zeros((nv, 3))
+        typ = np.zeros(nv, dtype=np.int32)
+        self._check(self._L.mfs_get_strengths(self._h, None, _dp(pos), _ip(typ)))
+        return pos, typ
+
+    def collocation(self):
+        s = self.sizes()
+        x = np.zeros((s.n_colloc, 3))
+        w = np.zeros(s.n_colloc)
+        o = np.zeros(s.n_colloc, dtype=np.int32)
+        self._check(self._L.mfs_get_collocation(self._h, _dp(x), _dp(w), _ip(o)))
+        return x, w, o
+
+    def rhs(self):
+        s = self.sizes()
+        b = np.zeros(3 * s.n_colloc)
+        self._check(self._L.mfs_get_rhs(self._h, _dp(b)))
+        return b
+
+    def apply_operator(self, mu, precision=FP64):
+        mu = _f64(mu)
+        out = np.zeros_like(mu)
+        self._check(self._L.mfs_apply_operator(self._h, int(precision), _dp(mu), _dp(out)))
+        return out
+
+    def apply_precond(self, mu, precision=FP64):
+        mu = _f64(mu)
+        out = np.zeros(self.sizes().n_unknowns)
+        self._check(self._L.mfs_apply_precond(self._h, int(precision), _dp(mu), _dp(out)))
+        return out
+
+    def apply_pairs(self, lam_hat, mu, precision=FP64):
+        lam_hat = _f64(lam_hat)
+        mu = _f64(mu)
+        out = np.zeros_like(mu)
+        self._check(self._L.mfs_apply_pairs(self._h, int(precision), _dp(lam_hat), _dp(mu), _dp(out)))
+        return out
