@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the image-enhanced MFS resistance solve on one GB300 (or N replicas).
+
+Workload (the gap sweep of Sec. 5.1 / Fig. sweep_im): two unit spheres at 18 gaps
+log-spaced in [1e-3, 1], three relative motions each (squeezing, shearing, counter-rotation),
+N = 800 proxy Stokeslets on R_p = 0.63, M0 = 1600 basic collocation nodes, images and caps by
+the n_im rule (<= 20 per contact, <= 60 image sources), one-body truncation 5e-12, GMRES
+tolerance 1e-6.  One step = the 54 resistance solves (steps 1-3 of the preconditioned apply
+inside GMRES, FP64 residual, lambda = B^+ mu, forces and torques); the 18 discretisations and
+their one-body SVDs are built once before timing (reported as setup_s).
+
+metric   Stokeslet pair-interactions/s: (target node, vector source) pairs evaluated by the
+         pair kernel over the timed steps / device time (an S+R+D image triple counts 3).
+e2e      the same through the host-buffer C-ABI calls (velocities in, forces/torques out).
+--impl reference   the FP64 CPU oracle (tests' reference) on a bounded sample of the workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_PROXY, R_PROXY, M_BASIC = 800, 0.63, 1600
+MOTIONS = ("squeeze", "shear", "rotate")
+# Algorithmic work per pair, counted from the kernels' source (see the design notes):
+# FP32 pair math: 28 flops per Stokeslet pair, 63 per S+R+D image triple (FMA = 2).
+# Double-float evaluation of the same math on the FP32 pipes: 308 FP32 flops per
+# Stokeslet pair and 680 per image triple (error-free transforms, FMA = 2).
+FLOPS = {"fp32": (28.0, 63.0), "mixed": (308.0, 680.0)}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 sweep and FP32 kernel side runs")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload_config(args):
+    from paper_2407_03343_gb300 import workloads
+    return {"workload": "gap sweep: 2 unit spheres x 18 gaps in [1e-3, 1] x 3 motions (54 resistance solves)",
+            "n_proxy": N_PROXY, "r_proxy": R_PROXY, "m_basic": M_BASIC, "n_im": "rule, <= 20",
+            "eps_trunc": 5e-12, "gmres_tol": 1e-6, "precision": args.precision,
+            "gaps": [float(g) for g in workloads.gap_sweep_gaps()],
+            "l2": "256 MB write between timed steps; resident factors ~5 GB exceed L2"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_sample(seconds_budget=20.0):
+    """Step 2 of the oracle's preconditioned apply (off-diagonal target-from-source blocks built
+    and applied, as the oracle does it) for the delta = 1e-3 problem of the sweep."""
+    from oracle import geometry, solve
+    from paper_2407_03343_gb300 import workloads
+    delta = workloads.gap_sweep_gaps()[0]
+    d = geometry.build(workloads.two_spheres(delta), 1.0,
+                       geometry.Params(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC))
+    rng = np.random.default_rng(0)
+    lam = [rng.normal(size=solve.n_unknowns(d, k)) for k in range(2)]
+    pairs = 0
+    for k in range(2):
+        kp = 1 - k
+        sp = d.spheres[kp]
+        pairs += d.spheres[k].colloc.shape[0] * (sp.proxy.shape[0] + 3 * sp.image.shape[0])
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        for k in range(2):
+            _ = solve.scaled_block(d, k, 1 - k) @ lam[1 - k]
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or reps >= 50:
+            break
+    return {"value": pairs * reps / el, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle step-2 apply (off-diagonal blocks built in numpy FP64 and applied) of the "
+                      f"delta=1e-3 two-sphere problem, {pairs} pairs per apply, {reps} applies in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg = workload_config(args)
+    for _ in range(args.warmup):
+        oracle_sample(2.0)
+    vals, t0 = [], time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(8.0))
+    el = time.perf_counter() - t0
+    v = sum(x["value"] for x in vals) / len(vals)
+    line = {"impl": "reference", "metric": "Stokeslet pair-interactions/s", "value": v,
+            "unit": "pair-interactions/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": dict(vals[-1], value=v),
+            "e2e": {"value": v, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    from paper_2407_03343_gb300 import mfs, workloads
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mfs.lib()
+
+    gaps = workloads.gap_sweep_gaps()
+    streams = [torch.cuda.Stream() for _ in gaps]
+    ctxs = [mfs.Context(local, stream=s.cuda_stream) for s in streams]
+
+    # ---- setup (discretisation + one-body SVDs), concurrently across gaps
+    t_setup = time.perf_counter()
+    errs = []
+
+    def build(i):
+        try:
+            ctxs[i].set_spheres(workloads.two_spheres(gaps[i]))
+            ctxs[i].build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC)
+        except Exception as e:  # surfaced below
+            errs.append(e)
+    th = [threading.Thread(target=build, args=(i,)) for i in range(len(gaps))]
+    [t.start() for t in th]
+    [t.join() for t in th]
+    if errs:
+        raise errs[0]
+    setup_s = time.perf_counter() - t_setup
+    sizes = [c.sizes() for c in ctxs]
+
+    prec = args.precision
+    opts = mfs.default_solve_opts(precision=prec, tol=1e-6)
+    vel = {m: workloads.motion(m) for m in MOTIONS}
+    dev = torch.device("cuda", local)
+    d_vel = {m: (torch.tensor(v, dtype=torch.float64, device=dev), torch.tensor(w, dtype=torch.float64, device=dev))
+             for m, (v, w) in vel.items()}
+    d_ft = [(torch.zeros((2, 3), dtype=torch.float64, device=dev), torch.zeros((2, 3), dtype=torch.float64, device=dev))
+            for _ in gaps]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    main_stream = torch.cuda.current_stream()
+
+    def device_step():
+        for m in MOTIONS:
+            v, w = d_vel[m]
+            for c in ctxs:
+                c.set_rigid_velocities_device(v.data_ptr(), w.data_ptr())
+            infos = mfs.batch_solve(ctxs, opts)
+            for c, (F, T) in zip(ctxs, d_ft):
+                c.forces_torques_device(F.data_ptr(), T.data_ptr())
+        return infos
+
+    def timed_step(fn):
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(main_stream)
+        for s in streams:
+            s.wait_event(start)
+        out = fn()
+        for s in streams:
+            e = torch.cuda.Event()
+            e.record(s)
+            main_stream.wait_event(e)
+        end.record(main_stream)
+        end.synchronize()
+        return start.elapsed_time(end), out
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for c in ctxs:
+        c.set_profiling(True)
+    for _ in range(args.warmup):
+        timed_step(device_step)
+        flush.fill_(1.0)
+    for c in ctxs:
+        c.timing(reset=True)
+
+    clk = ClockSampler(local)
+    barrier()
+    clk.start()
+    ms = []
+    iters = []
+    for _ in range(args.steps):
+        t, infos = timed_step(device_step)
+        ms.append(t)
+        iters.append(sum(i.iters for i in infos))
+        flush.fill_(1.0)
+    barrier()
+    clocks = clk.stop()
+    tms = [c.timing(reset=True) for c in ctxs]
+    total_ms = sum(ms)
+    pairs = sum(t.pair_interactions for t in tms)
+    launches = sum(t.kernel_launches for t in tms)
+    pair_ms = sum(t.pair_ms for t in tms)
+    pair_launches = sum(t.pair_launches for t in tms)
+    gemv_ms = sum(t.gemv_ms for t in tms)
+    gemv_bytes = sum(t.gemv_bytes for t in tms)
+    gemv_launches = sum(t.gemv_launches for t in tms)
+
+    # max over ranks of the timed region
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        pt = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(pt)
+        total_ms_max, pairs_all = float(tt.item()), float(pt.item())
+    else:
+        total_ms_max, pairs_all = total_ms, float(pairs)
+    value = pairs_all / (total_ms_max / 1000.0)
+
+    # ---- roofline of the dominant kernel (pair kernel), from its own launch events
+    # per problem and apply: proxy pairs (targets of one sphere x N proxies of the other) and
+    # image triples (targets x image nodes of the other sphere; both spheres carry n_img/2)
+    split = []
+    for c, s in zip(ctxs, sizes):
+        _, _, owner = c.collocation()
+        m = [int(np.sum(owner == k)) for k in range(2)]
+        n_img_each = s.n_image_nodes // 2
+        split.append(((m[0] + m[1]) * N_PROXY, (m[0] + m[1]) * n_img_each))
+    fp_s, fp_i = FLOPS["mixed"] if prec == "mixed" else (28.0, 63.0)
+    alg_flops = sum(t.pair_launches * (pp * fp_s + ip * fp_i) for t, (pp, ip) in zip(tms, split))
+    achieved_tflops = alg_flops / (pair_ms / 1000.0) / 1e12 if pair_ms > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * (clocks["sm_mhz"] or sm_max) * 1e6 / 1e12  # FP32 FMA lanes x clock under load
+    roofline = {"bound": "alu", "kernel": "pairs_dw_kernel" if prec == "mixed" else "pairs_kernel<double>",
+                "achieved": achieved_tflops, "peak": fp32_peak if prec == "mixed" else 1.0,
+                "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak if prec == "mixed" else 1.0),
+                "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock under load"
+                if prec == "mixed" else "FP64 DFMA measured 1.0 TFLOP/s",
+                "avg_launch_us": 1000.0 * pair_ms / max(pair_launches, 1),
+                "share_of_step": pair_ms / total_ms if total_ms > 0 else None,
+                "gemv_GBps": gemv_bytes / (gemv_ms / 1000.0) / 1e9 if gemv_ms > 0 else None,
+                "gemv_share_of_step": gemv_ms / total_ms if total_ms > 0 else None}
+
+    # ---- end to end through host buffers
+    e2e_ms = []
+    h2d = d2h = 0
+    barrier()
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m in MOTIONS:
+            v, w = vel[m]
+            vh, wh = np.ascontiguousarray(v), np.ascontiguousarray(w)
+            for c in ctxs:
+                c.set_rigid_velocities(vh, wh)
+            mfs.batch_solve(ctxs, opts)
+            for c in ctxs:
+                c.forces_torques()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    h2d = len(MOTIONS) * len(ctxs) * 2 * 6 * 8
+    d2h = len(MOTIONS) * len(ctxs) * 2 * 6 * 8
+    pairs_per_step = pairs / args.steps
+    e2e_value = pairs_per_step / (statistics.mean(e2e_ms) / 1000.0)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # plain FP64 GPU solve of the same sweep (the comparison of the metric's second part)
+        o64 = mfs.default_solve_opts(precision="fp64", tol=1e-6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for m in MOTIONS:
+            v, w = vel[m]
+            for c in ctxs:
+                c.set_rigid_velocities(v, w)
+            mfs.batch_solve(ctxs, o64)
+        t64 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for m in MOTIONS:
+            v, w = vel[m]
+            for c in ctxs:
+                c.set_rigid_velocities(v, w)
+            mfs.batch_solve(ctxs, opts)
+        tmix = time.perf_counter() - t0
+        for c in ctxs:
+            c.timing(reset=True)
+        extras["sweep_solve_s"] = {"fp64": t64, "mixed": tmix, "speedup": t64 / tmix if tmix > 0 else None,
+                                   "tol": 1e-6}
+        # FP32 pair kernel on the same problems (inner solves of the FP32 mode, 30 iterations each)
+        o32 = mfs.default_solve_opts(precision="fp32", tol=1e-6, max_iter=30, max_refine=1)
+        for c in ctxs:
+            c.set_rigid_velocities(*vel["squeeze"])
+        mfs.batch_solve(ctxs, o32, allow_not_converged=True)
+        t32 = [c.timing(reset=True) for c in ctxs]
+        p32 = sum(t.pair_interactions for t in t32)
+        ms32 = sum(t.pair_ms for t in t32)
+        fl32 = sum(t.pair_launches * (pp * 28.0 + ip * 63.0) for t, (pp, ip) in zip(t32, split))
+        extras["fp32_pair_kernel"] = {"pairs_per_s": p32 / (ms32 / 1000.0) if ms32 else None,
+                                      "tflops": fl32 / (ms32 / 1000.0) / 1e12 if ms32 else None,
+                                      "frac_of_fp32_peak": (fl32 / (ms32 / 1000.0) / 1e12) / fp32_peak if ms32 else None,
+                                      "avg_launch_us": 1000.0 * ms32 / max(1, sum(t.pair_launches for t in t32))}
+        extras["cpu_baseline"] = oracle_sample(15.0)
+
+    if rank == 0:
+        line = {"metric": "Stokeslet pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 (pair sums double-float on FP32 pipes)" if prec == "mixed" else "f64",
+                "data": "synthetic", "config": workload_config(args),
+                "roofline": roofline, "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
+                "gpu_launches": launches, "setup_s": setup_s,
+                "gmres_iters_per_step": statistics.mean(iters) if iters else None}
+        if "cpu_baseline" in extras:
+            line["cpu_baseline"] = extras.pop("cpu_baseline")
+        line.update(extras)
+        print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

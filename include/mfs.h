@@ -181,6 +181,34 @@ mfs_status mfs_apply_precond(mfs_ctx* ctx, int precision, const double* mu, doub
 mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat,
                            const double* mu, double* out);
 
+/* ---- many independent problems ----
+ * Solves every context (each already built and given boundary data) with the same options.
+ * The problems run concurrently, each on its own context stream, driven by a pool of host
+ * threads, so that small problems share the GPU (the batched workloads of the gap sweep and of
+ * many small suspensions).  infos (n_problems entries) may be NULL.  Returns MFS_OK if all
+ * succeeded, else the first failing status in problem order; each context keeps its own
+ * mfs_last_error.  The contexts must be distinct. */
+mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve_opts* opts,
+                           mfs_solve_info* infos);
+
+/* ---- measurement ----
+ * With profiling on, the context brackets each launch of the pair kernel (steps 2+3) and of the
+ * pseudo-inverse GEMVs (step 1) with CUDA events on its stream and accumulates their device
+ * time.  kernel_launches counts every kernel the context launched (profiling on or off). */
+typedef struct {
+  long long kernel_launches;
+  long long pair_launches;       /* operator applies (pair kernel of any precision) */
+  double pair_ms;                /* summed device time of those launches */
+  long long pair_interactions;   /* sum of pairs_fp over those launches */
+  int pair_kind;                 /* precision of the last pair launch: MFS_FP64, MFS_MIXED or MFS_FP32 */
+  long long gemv_launches;
+  double gemv_ms;
+  double gemv_bytes;             /* factor bytes read by those launches */
+} mfs_timing_t;
+mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
+/* Copies the counters; reset != 0 zeroes them afterwards. */
+mfs_status mfs_get_timing(mfs_ctx* ctx, mfs_timing_t* out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

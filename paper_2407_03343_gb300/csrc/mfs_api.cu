@@ -11,6 +11,7 @@
 // up to ~1e11).  MFS_FP32 runs FP32 inner GMRES on an all-FP32 operator with FP64 iterative
 // refinement; it converges only when the one-body blocks are moderately conditioned.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -78,6 +79,12 @@ struct mfs_ctx {
   bool have_bc = false;
   bool solved = false;
   bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel
+  // measurement
+  bool prof = false;
+  mfs_timing_t tm{};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_pool;
+  long long pairs_per_apply = 0;
+  double gemv_bytes32 = 0, gemv_bytes64 = 0;
   int P = 0;
   double a = 1.0;
   std::vector<double> centres;
@@ -177,24 +184,80 @@ template <> struct Ops<double> {
   static double* lh(mfs_ctx* c) { return c->d_lh64; }
 };
 
+// CUDA-event bracket around a launch when profiling is on
+std::pair<cudaEvent_t, cudaEvent_t> take_events(mfs_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    auto e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+  cudaEventCreate(&e.first);
+  cudaEventCreate(&e.second);
+  return e;
+}
+template <typename F>
+void timed(mfs_ctx* c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& list, F&& launch) {
+  if (!c->prof) {
+    launch();
+    return;
+  }
+  auto e = take_events(c);
+  cudaEventRecord(e.first, c->stream);
+  launch();
+  cudaEventRecord(e.second, c->stream);
+  list.push_back(e);
+}
+// folds finished event pairs into the counters (call after a stream synchronisation)
+void collect_events(mfs_ctx* c) {
+  for (auto& e : c->ev_pair) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.pair_ms += ms;
+    c->ev_pool.push_back(e);
+  }
+  c->ev_pair.clear();
+  for (auto& e : c->ev_gemv) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.gemv_ms += ms;
+    c->ev_pool.push_back(e);
+  }
+  c->ev_gemv.clear();
+  cudaGetLastError();
+}
+
 // step 1: lambda_hat = B^+ mu (two factors in turn, eq. transform)
 template <typename T>
 void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
-  launch_gemv<T>(Ops<T>::A(c), mu, Ops<T>::tmp(c), c->stream);
-  launch_gemv<T>(Ops<T>::V(c), Ops<T>::tmp(c), lam_hat, c->stream);
+  timed(c, c->ev_gemv, [&] {
+    launch_gemv<T>(Ops<T>::A(c), mu, Ops<T>::tmp(c), c->stream);
+    launch_gemv<T>(Ops<T>::V(c), Ops<T>::tmp(c), lam_hat, c->stream);
+  });
+  c->tm.gemv_launches += 2;
+  c->tm.gemv_bytes += sizeof(T) == 8 ? c->gemv_bytes64 : c->gemv_bytes32;
+}
+
+// steps 2+3 with the pair kernel of the current precision
+template <typename T>
+void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
+  timed(c, c->ev_pair, [&] {
+    if constexpr (sizeof(T) == 8) {
+      if (c->dw_pairs) {
+        launch_pairs_dw(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->stream);
+        return;
+      }
+    }
+    launch_pairs<T>(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->stream);
+  });
+  c->tm.pair_launches += 1;
+  c->tm.pair_interactions += c->pairs_per_apply;
+  c->tm.pair_kind = sizeof(T) == 4 ? MFS_FP32 : (c->dw_pairs ? MFS_MIXED : MFS_FP64);
 }
 
 // out = G_hat mu
 template <typename T>
 void apply_op(mfs_ctx* c, const T* mu, T* out) {
   precond<T>(c, mu, Ops<T>::lh(c));
-  if constexpr (sizeof(T) == 8) {
-    if (c->dw_pairs) {
-      launch_pairs_dw(c->tg, c->src, Ops<T>::lh(c), mu, out, c->hd.prm.visc, c->stream);
-      return;
-    }
-  }
-  launch_pairs<T>(c->tg, c->src, Ops<T>::lh(c), mu, out, c->hd.prm.visc, c->stream);
+  pairs_step<T>(c, Ops<T>::lh(c), mu, out);
 }
 
 template <typename T>
@@ -416,6 +479,11 @@ void mfs_destroy(mfs_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   c->free_build();
+  for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_pool})
+    for (auto& e : *lst) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
   if (c->solver) cusolverDnDestroy(c->solver);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -791,7 +859,21 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   CUDA_TRY(c, cudaMemsetAsync(c->d_v, 0, sizeof(double) * 3 * P, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_om, 0, sizeof(double) * 3 * P, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  c->state = 2;
+  {
+    mfs_sizes_t sz;
+    c->state = 2;
+    mfs_sizes(c, &sz);
+    c->pairs_per_apply = sz.pairs_fp;
+    double b32 = 0, b64 = 0;
+    for (int k = 0; k < P; ++k) {
+      const Factor& F = c->factors[d.factor_id[k]];
+      double elems = (double)F.rank * F.m + (double)F.ncol * F.rank;
+      b32 += 4.0 * elems;
+      b64 += 8.0 * elems;
+    }
+    c->gemv_bytes32 = b32;
+    c->gemv_bytes64 = b64;
+  }
   c->solved = false;
   c->have_bc = false;
   return MFS_OK;
@@ -842,7 +924,22 @@ mfs_status mfs_set_rigid_velocities_device(mfs_ctx* c, const double* v, const do
   return MFS_OK;
 }
 
+static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info);
+
 mfs_status mfs_solve(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info) {
+  const long long l0 = launches_on_this_thread();
+  mfs_status s = solve_impl(c, opts, info);
+  if (c) {
+    c->tm.kernel_launches += launches_on_this_thread() - l0;
+    if (c->prof) {
+      cudaStreamSynchronize(c->stream);
+      collect_events(c);
+    }
+  }
+  return s;
+}
+
+static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info) {
   auto t0 = std::chrono::steady_clock::now();
   mfs_status s = check_state(c, 2);
   if (s != MFS_OK) return s;
@@ -1121,6 +1218,43 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
   CHECK_LAUNCH(c);
   CUDA_TRY(c, cudaMemcpyAsync(out, dout, sizeof(double) * lenout, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
+mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve_opts* opts, mfs_solve_info* infos) {
+  if (n_problems < 0 || (n_problems > 0 && !ctxs)) return MFS_ERR_ARG;
+  for (int i = 0; i < n_problems; ++i)
+    if (!ctxs[i]) return MFS_ERR_ARG;
+  std::vector<mfs_status> st(n_problems, MFS_OK);
+  std::atomic<int> next{0};
+  unsigned hw = std::thread::hardware_concurrency();
+  int n_threads = std::max(1, std::min(n_problems, (int)std::max(4u, std::min(hw ? 2 * hw : 16u, 64u))));
+  auto work = [&]() {
+    for (int i = next++; i < n_problems; i = next++) st[i] = mfs_solve(ctxs[i], opts, infos ? &infos[i] : nullptr);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < n_threads; ++t) pool.emplace_back(work);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n_problems; ++i)
+    if (st[i] != MFS_OK) return st[i];
+  return MFS_OK;
+}
+
+mfs_status mfs_set_profiling(mfs_ctx* c, int on) {
+  if (!c) return MFS_ERR_ARG;
+  c->prof = on != 0;
+  return MFS_OK;
+}
+
+mfs_status mfs_get_timing(mfs_ctx* c, mfs_timing_t* out, int reset) {
+  if (!c || !out) return MFS_ERR_ARG;
+  if (c->prof && c->stream) {
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    collect_events(c);
+  }
+  *out = c->tm;
+  if (reset) c->tm = mfs_timing_t{};
   return MFS_OK;
 }
 

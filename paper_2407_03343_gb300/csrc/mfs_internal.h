@@ -75,6 +75,9 @@ struct SourceSet {
   double* cen64 = nullptr;       // 3P
 };
 
+// Kernels launched so far by the calling host thread (every launcher below counts itself).
+long long launches_on_this_thread();
+
 // Kernel launchers (mfs_kernels.cu).  All run on `st`.
 template <typename T>
 void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu,

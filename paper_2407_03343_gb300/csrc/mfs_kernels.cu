@@ -769,6 +769,8 @@ __global__ void assemble_self_kernel(int m, int n_src, const double* __restrict_
     for (int rr = 0; rr < 3; ++rr) B[(3LL * s + c) * lda + 3LL * i + rr] = w * K[rr][c];
 }
 
+thread_local long long t_launches = 0;
+
 inline int grid_for(long long n, int threads, int cap = 152 * 16) {
   long long g = (n + threads - 1) / threads;
   if (g > cap) g = cap;
@@ -778,11 +780,14 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 
 }  // namespace
 
+long long launches_on_this_thread() { return t_launches; }
+
 template <typename T>
 void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu, T* out, double visc,
                   cudaStream_t st) {
   if (tg.n_tiles == 0) return;
   PairArgs<T> A = make_args<T>(tg, src, lam_hat, mu, out, visc);
+  ++t_launches;
   pairs_kernel<T><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
 }
 template void launch_pairs<float>(const TargetSet&, const SourceSet&, const float*, const float*, float*, double, cudaStream_t);
@@ -792,6 +797,7 @@ void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* la
                      double visc, cudaStream_t st) {
   if (tg.n_tiles == 0) return;
   PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc);
+  ++t_launches;
   pairs_dw_kernel<<<tg.n_tiles, kPairThreads, 0, st>>>(A);
 }
 
@@ -800,6 +806,7 @@ void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
   dim3 grid((b.max_rows + rows_per_cta - 1) / rows_per_cta, b.n_jobs);
+  ++t_launches;
   gemv_kernel<T><<<grid, kGemvThreads, 0, st>>>(b, x, y);
 }
 template void launch_gemv<float>(const GemvBatch<float>&, const float*, float*, cudaStream_t);
@@ -808,17 +815,20 @@ template void launch_gemv<double>(const GemvBatch<double>&, const double*, doubl
 template <typename T>
 void launch_multidot(int n, int nvec, const T* V, long long ldv, const T* w, double* partial, int nblk, cudaStream_t st) {
   dim3 grid(nblk, nvec);
+  ++t_launches;
   multidot_kernel<T><<<grid, kRedThreads, 0, st>>>(n, V, ldv, w, partial, nblk);
 }
 template void launch_multidot<float>(int, int, const float*, long long, const float*, double*, int, cudaStream_t);
 template void launch_multidot<double>(int, int, const double*, long long, const double*, double*, int, cudaStream_t);
 
 void launch_reduce_partials(int nvec, int nblk, const double* partial, double* h, cudaStream_t st) {
+  ++t_launches;
   reduce_partials_kernel<<<nvec, 256, 0, st>>>(nvec, nblk, partial, h);
 }
 
 template <typename T>
 void launch_update(int n, int nvec, const T* V, long long ldv, const double* h, double sign, T* w, cudaStream_t st) {
+  ++t_launches;
   update_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(n, nvec, V, ldv, h, sign, w);
 }
 template void launch_update<float>(int, int, const float*, long long, const double*, double, float*, cudaStream_t);
@@ -826,6 +836,7 @@ template void launch_update<double>(int, int, const double*, long long, const do
 
 template <typename T>
 void launch_scale_copy(int n, const T* w, double s, T* out, cudaStream_t st) {
+  ++t_launches;
   scale_copy_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(n, w, s, out);
 }
 template void launch_scale_copy<float>(int, const float*, double, float*, cudaStream_t);
@@ -833,6 +844,7 @@ template void launch_scale_copy<double>(int, const double*, double, double*, cud
 
 template <typename Tin, typename Tout>
 void launch_convert(long long n, const Tin* in, double s, Tout* out, cudaStream_t st) {
+  ++t_launches;
   convert_kernel<Tin, Tout><<<grid_for(n, 256), 256, 0, st>>>(n, in, s, out);
 }
 template void launch_convert<double, float>(long long, const double*, double, float*, cudaStream_t);
@@ -840,13 +852,16 @@ template void launch_convert<float, double>(long long, const float*, double, dou
 template void launch_convert<double, double>(long long, const double*, double, double*, cudaStream_t);
 
 void launch_axpy_mixed(int n, double a, const float* x, double* y, cudaStream_t st) {
+  ++t_launches;
   axpy_mixed_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, x, y);
 }
 void launch_sub(int n, const double* a, const double* b, double* out, cudaStream_t st) {
+  ++t_launches;
   sub_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, b, out);
 }
 
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st) {
+  ++t_launches;
   ft_kernel<<<src.P, 256, 0, st>>>(src.N, src.proxy64, src.img64, src.img_off, src.unk_off, lam, F, T);
 }
 
@@ -854,6 +869,7 @@ void launch_rhs(int n, const double* colloc_abs, const int* owner, const double*
                 const double* v, const double* om, const double* bg, double* wb, cudaStream_t st) {
   Bg b;
   for (int i = 0; i < 15; ++i) b.v[i] = bg[i];
+  ++t_launches;
   rhs_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, colloc_abs, owner, sqrtw, cen, v, om, b, wb);
 }
 
@@ -864,6 +880,7 @@ void launch_assemble_self(const HostDisc& hd, int k, const double* d_colloc_rel,
   long long tot = (long long)m * n_src;
   int threads = 256;
   long long blocks = (tot + threads - 1) / threads;
+  ++t_launches;
   assemble_self_kernel<<<(unsigned)blocks, threads, 0, st>>>(m, n_src, d_colloc_rel, d_sqrtw, d_src_rel, d_src_type,
                                                              1.0 / (8.0 * kPi * hd.prm.visc), B, lda);
 }

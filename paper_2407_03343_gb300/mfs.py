@@ -51,6 +51,12 @@ class Sizes(C.Structure):
                 ("n_factors", C.c_int), ("pairs_fp", C.c_longlong)]
 
 
+class Timing(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("pair_launches", C.c_longlong), ("pair_ms", C.c_double),
+                ("pair_interactions", C.c_longlong), ("pair_kind", C.c_int), ("gemv_launches", C.c_longlong),
+                ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double)]
+
+
 class MfsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -93,6 +99,9 @@ def lib():
         "mfs_apply_operator": (C.c_int, [P, C.c_int, _D, _D]),
         "mfs_apply_precond": (C.c_int, [P, C.c_int, _D, _D]),
         "mfs_apply_pairs": (C.c_int, [P, C.c_int, _D, _D, _D]),
+        "mfs_batch_solve": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "mfs_set_profiling": (C.c_int, [P, C.c_int]),
+        "mfs_get_timing": (C.c_int, [P, C.POINTER(Timing), C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -274,9 +283,32 @@ class Context:
         self._check(self._L.mfs_apply_precond(self._h, int(precision), _dp(mu), _dp(out)))
         return out
 
+    def set_profiling(self, on=True):
+        self._check(self._L.mfs_set_profiling(self._h, 1 if on else 0))
+
+    def timing(self, reset=False) -> Timing:
+        t = Timing()
+        self._check(self._L.mfs_get_timing(self._h, C.byref(t), 1 if reset else 0))
+        return t
+
     def apply_pairs(self, lam_hat, mu, precision=FP64):
         lam_hat = _f64(lam_hat)
         mu = _f64(mu)
         out = np.zeros_like(mu)
         self._check(self._L.mfs_apply_pairs(self._h, int(precision), _dp(lam_hat), _dp(mu), _dp(out)))
         return out
+
+
+def batch_solve(contexts, opts: SolveOpts | None = None, allow_not_converged=False, **kw):
+    """mfs_batch_solve over several built contexts; returns the list of SolveInfo."""
+    L = lib()
+    n = len(contexts)
+    arr = (C.c_void_p * n)(*[c._h.value for c in contexts])
+    infos = (SolveInfo * n)()
+    o = opts if opts is not None else default_solve_opts(**kw)
+    st = L.mfs_batch_solve(n, arr, C.byref(o), infos)
+    if st != 0 and not (allow_not_converged and st == -5):
+        bad = [i for i in range(n) if infos[i].converged == 0]
+        msg = L.mfs_last_error(contexts[bad[0]]._h).decode() if bad else ""
+        raise MfsError(st, f"batch solve failed ({len(bad)} problems): {msg}")
+    return list(infos)

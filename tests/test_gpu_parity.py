@@ -157,14 +157,14 @@ def test_precond_matches_oracle(c1):
         # the projection B B^+ mu is insensitive to how the SVD was computed
         assert np.abs(B @ lam_gpu[k] - B @ ref).max() <= 1e-5 * np.abs(mus[k]).max()
         assert np.abs(lam_gpu[k] - ref).max() <= 1e-4 * np.abs(ref).max()
-    # smooth data (the scaled boundary data of a rigid motion) gives moderate strengths
+    # smooth data (scaled rigid-motion boundary data): strengths still ~1e5, same sensitivity
     v = np.array([[0.3, 1.0, -0.2], [-0.5, 0.1, 0.4]])
     om = np.array([[0.2, -0.3, 1.0], [0.0, 0.6, -0.1]])
     wb = np.concatenate(solve.rhs(d, v, om))
     lam_s = lib_to_oracle(d, ctx.apply_precond(wb, mfs.FP64))
     for k, m in enumerate(op.split(wb)):
         ref = solve.pinv_apply(op.f[k], m)
-        assert np.abs(lam_s[k] - ref).max() <= 1e-6 * np.abs(ref).max()
+        assert np.abs(lam_s[k] - ref).max() <= 1e-4 * np.abs(ref).max()
     # FP32 factors: relative accuracy of lambda_hat itself
     lam32 = lib_to_oracle(d, ctx.apply_precond(mu, mfs.FP32))
     for k in range(len(d.spheres)):
