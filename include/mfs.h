@@ -181,6 +181,23 @@ mfs_status mfs_apply_precond(mfs_ctx* ctx, int precision, const double* mu, doub
 mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat,
                            const double* mu, double* out);
 
+/* ---- step 1 without any device allocation ----
+ * The paper has no counterpart to this call; it serves callers that cannot allocate device
+ * memory while they run: an application that owns all device memory through its own pool and
+ * forbids cudaMalloc/cudaFree (which also synchronise the device) inside its time-stepping
+ * loop, or code on a latency-critical path.  It computes the same lambda_hat = B_k^+ mu_k for
+ * every sphere as mfs_apply_precond with MFS_FP64, but from DEVICE buffers the caller owns:
+ * d_mu (3*n_colloc doubles) in, d_lambda_hat (n_unknowns doubles) out.  The intermediate
+ * Sigma^+ U^T mu lives in a fixed array of 2^21 doubles (16 MiB) that the library reserves on
+ * every GPU that loads it, until the process exits; a context whose summed retained ranks
+ * exceed that size gets MFS_ERR_ARG.  The call allocates nothing (the context's factors were
+ * allocated by mfs_build).  Its first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other threads, contexts or streams) race and must be serialised by the
+ * caller.  Nothing in the array needs clearing; each call overwrites what it reads.  Returns
+ * after the context's stream has drained. */
+mfs_status mfs_apply_precond_noalloc(mfs_ctx* ctx, const double* d_mu, double* d_lambda_hat);
+
 /* ---- many independent problems ----
  * Solves every context (each already built and given boundary data) with the same options.
  * The problems run concurrently, each on its own context stream, driven by a pool of host

@@ -1258,6 +1258,48 @@ mfs_status mfs_get_timing(mfs_ctx* c, mfs_timing_t* out, int reset) {
   return MFS_OK;
 }
 
+// ---- pseudo-inverse apply that allocates nothing
+// Scratch for the intermediate Sigma^+ U^T mu of every sphere, resident on each GPU that
+// loads the library until the process exits.  Host code reaches it only through the device
+// address looked up below; the array's host-side name is a stand-in, not a device pointer.
+constexpr long long kNoAllocScratch = 1LL << 21;  // doubles (16 MiB)
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+static std::mutex g_noalloc_mtx;
+static double* g_noalloc_ptr[64] = {nullptr};
+
+mfs_status mfs_apply_precond_noalloc(mfs_ctx* c, const double* d_mu, double* d_lambda_hat) {
+  mfs_status s = check_state(c, 2);  // also makes the context's device current
+  if (s != MFS_OK) return s;
+  if (!d_mu || !d_lambda_hat) return c->fail(MFS_ERR_ARG, "null device pointer");
+  if (c->tmp_len > kNoAllocScratch)
+    return c->fail(MFS_ERR_ARG, "mfs_apply_precond_noalloc: the summed retained ranks (" + std::to_string(c->tmp_len) +
+                                    ") exceed its fixed scratch of " + std::to_string(kNoAllocScratch) + " doubles");
+  if (c->device < 0 || c->device >= 64) return c->fail(MFS_ERR_ARG, "device index out of range for the static scratch table");
+  double* scratch = nullptr;
+  {
+    // first call on this device: resolve the array's device address with the device current
+    std::lock_guard<std::mutex> g(g_noalloc_mtx);
+    if (!g_noalloc_ptr[c->device]) {
+      double* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        return c->fail(MFS_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+      }
+      g_noalloc_ptr[c->device] = ptr;
+    }
+    scratch = g_noalloc_ptr[c->device];
+  }
+  // every scratch entry that the second GEMV reads is written by the first one of the same
+  // call, so nothing has to be cleared between calls
+  launch_gemv<double>(c->gA64, d_mu, scratch, c->stream);
+  launch_gemv<double>(c->gV64, scratch, d_lambda_hat, c->stream);
+  CHECK_LAUNCH(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
+
 mfs_status mfs_apply_operator(mfs_ctx* c, int precision, const double* mu, double* out) {
   return run_step(c, precision, 0, mu, nullptr, out);
 }

@@ -99,6 +99,7 @@ def lib():
         "mfs_apply_operator": (C.c_int, [P, C.c_int, _D, _D]),
         "mfs_apply_precond": (C.c_int, [P, C.c_int, _D, _D]),
         "mfs_apply_pairs": (C.c_int, [P, C.c_int, _D, _D, _D]),
+        "mfs_apply_precond_noalloc": (C.c_int, [P, P, P]),
         "mfs_batch_solve": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "mfs_set_profiling": (C.c_int, [P, C.c_int]),
         "mfs_get_timing": (C.c_int, [P, C.POINTER(Timing), C.c_int]),
@@ -282,6 +283,10 @@ class Context:
         out = np.zeros(self.sizes().n_unknowns)
         self._check(self._L.mfs_apply_precond(self._h, int(precision), _dp(mu), _dp(out)))
         return out
+
+    def apply_precond_noalloc(self, d_mu_ptr: int, d_lambda_hat_ptr: int):
+        """Step 1 on caller-owned device buffers, without any device allocation."""
+        self._check(self._L.mfs_apply_precond_noalloc(self._h, C.c_void_p(d_mu_ptr), C.c_void_p(d_lambda_hat_ptr)))
 
     def set_profiling(self, on=True):
         self._check(self._L.mfs_set_profiling(self._h, 1 if on else 0))
