@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 sweep and FP32 kernel side runs")
+    ap.add_argument("--kernel-case", type=int, default=0,
+                    help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
     return ap.parse_args()
 
 
@@ -203,6 +205,15 @@ def main():
 
     prec = args.precision
     opts = mfs.default_solve_opts(precision=prec, tol=1e-6)
+    if args.kernel_case:
+        v, w = workloads.motion("squeeze")
+        for c in ctxs:
+            c.set_rigid_velocities(v, w)
+        mfs.batch_solve(ctxs, mfs.default_solve_opts(precision=prec, tol=1e-12, max_iter=args.kernel_case,
+                                                     max_refine=1), allow_not_converged=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": args.kernel_case, "setup_s": setup_s}))
+        return 0
     vel = {m: workloads.motion(m) for m in MOTIONS}
     dev = torch.device("cuda", local)
     d_vel = {m: (torch.tensor(v, dtype=torch.float64, device=dev), torch.tensor(w, dtype=torch.float64, device=dev))
@@ -284,17 +295,11 @@ def main():
         total_ms_max, pairs_all = total_ms, float(pairs)
     value = pairs_all / (total_ms_max / 1000.0)
 
-    # ---- roofline of the dominant kernel (pair kernel), from its own launch events
-    # per problem and apply: proxy pairs (targets of one sphere x N proxies of the other) and
-    # image triples (targets x image nodes of the other sphere; both spheres carry n_img/2)
-    split = []
-    for c, s in zip(ctxs, sizes):
-        _, _, owner = c.collocation()
-        m = [int(np.sum(owner == k)) for k in range(2)]
-        n_img_each = s.n_image_nodes // 2
-        split.append(((m[0] + m[1]) * N_PROXY, (m[0] + m[1]) * n_img_each))
+    # ---- roofline of the dominant kernel (pair kernel), from its own launch events:
+    # algorithmic flops = proxy pairs x flops per Stokeslet pair + image node-pairs x flops per
+    # S+R+D triple, counted by the library for every pair launch in the timed steps
     fp_s, fp_i = FLOPS["mixed"] if prec == "mixed" else (28.0, 63.0)
-    alg_flops = sum(t.pair_launches * (pp * fp_s + ip * fp_i) for t, (pp, ip) in zip(tms, split))
+    alg_flops = sum(t.pair_proxy * fp_s + t.pair_image_nodes * fp_i for t in tms)
     achieved_tflops = alg_flops / (pair_ms / 1000.0) / 1e12 if pair_ms > 0 else 0.0
     peaks = {}
     try:
@@ -367,7 +372,7 @@ def main():
         t32 = [c.timing(reset=True) for c in ctxs]
         p32 = sum(t.pair_interactions for t in t32)
         ms32 = sum(t.pair_ms for t in t32)
-        fl32 = sum(t.pair_launches * (pp * 28.0 + ip * 63.0) for t, (pp, ip) in zip(t32, split))
+        fl32 = sum(t.pair_proxy * 28.0 + t.pair_image_nodes * 63.0 for t in t32)
         extras["fp32_pair_kernel"] = {"pairs_per_s": p32 / (ms32 / 1000.0) if ms32 else None,
                                       "tflops": fl32 / (ms32 / 1000.0) / 1e12 if ms32 else None,
                                       "frac_of_fp32_peak": (fl32 / (ms32 / 1000.0) / 1e12) / fp32_peak if ms32 else None,

@@ -199,12 +199,17 @@ mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat
 mfs_status mfs_apply_precond_noalloc(mfs_ctx* ctx, const double* d_mu, double* d_lambda_hat);
 
 /* ---- many independent problems ----
- * Solves every context (each already built and given boundary data) with the same options.
- * The problems run concurrently, each on its own context stream, driven by a pool of host
- * threads, so that small problems share the GPU (the batched workloads of the gap sweep and of
- * many small suspensions).  infos (n_problems entries) may be NULL.  Returns MFS_OK if all
- * succeeded, else the first failing status in problem order; each context keeps its own
- * mfs_last_error.  The contexts must be distinct. */
+ * Solves every context (each already built and given boundary data) with the same options,
+ * all at once: one GMRES runs in lockstep over the concatenation of the problems, each with
+ * its own Krylov coefficients, Hessenberg matrix and convergence test, and every kernel
+ * launch (pseudo-inverse GEMVs, pair sums, Gram-Schmidt) covers all problems still iterating.
+ * Restarts are iterative-refinement passes on the true residual.  The work runs on the first
+ * context's stream, ordered after work already queued on every context's stream; each
+ * context's stream then waits for the batch, and its outputs (forces/torques, strengths,
+ * velocity evaluation) are available as after mfs_solve.  MFS_FP32 falls back to solving
+ * the problems concurrently on their own streams.  All contexts must be on one device and
+ * distinct.  infos (n_problems entries) may be NULL.  Returns MFS_OK if all converged, else
+ * the first failing status in problem order; each context keeps its own mfs_last_error. */
 mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve_opts* opts,
                            mfs_solve_info* infos);
 
@@ -217,6 +222,8 @@ typedef struct {
   long long pair_launches;       /* operator applies (pair kernel of any precision) */
   double pair_ms;                /* summed device time of those launches */
   long long pair_interactions;   /* sum of pairs_fp over those launches */
+  long long pair_proxy;          /* of which (node, proxy Stokeslet) pairs */
+  long long pair_image_nodes;    /* and (node, image node) pairs, each an S+R+D triple */
   int pair_kind;                 /* precision of the last pair launch: MFS_FP64, MFS_MIXED or MFS_FP32 */
   long long gemv_launches;
   double gemv_ms;

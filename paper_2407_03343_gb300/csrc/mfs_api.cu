@@ -41,11 +41,19 @@ struct Factor {
   double* V64 = nullptr;  // ncol x ldV  (V)
   float* A32 = nullptr;
   float* V32 = nullptr;
+  float2* A2 = nullptr;   // (hi, lo) float pairs of A64 and V64 for the double-float GEMV
+  float2* V2 = nullptr;
 };
 
 // keep[i] is the SVD column index of the i-th retained singular triplet
+__device__ __forceinline__ float2 split2(double v) {
+  float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void pack_A_kernel(int r, int m, int ld, const double* __restrict__ U, const double* __restrict__ S,
-                              const int* __restrict__ keep, double* __restrict__ A64, float* __restrict__ A32) {
+                              const int* __restrict__ keep, double* __restrict__ A64, float* __restrict__ A32,
+                              float2* __restrict__ A2) {
   long long tot = (long long)r * ld;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     int i = (int)(id / ld), j = (int)(id % ld);
@@ -53,18 +61,20 @@ __global__ void pack_A_kernel(int r, int m, int ld, const double* __restrict__ U
     double v = j < m ? U[(long long)col * m + j] / S[col] : 0.0;
     A64[id] = v;
     A32[id] = (float)v;
+    A2[id] = split2(v);
   }
 }
 
 // VT is the column-major ncol x ncol matrix V^T returned by the SVD: V(row, i) = VT[row * ncol + i]
 __global__ void pack_V_kernel(int ncol, int r, int ld, const double* __restrict__ VT, const int* __restrict__ keep,
-                              double* __restrict__ V64, float* __restrict__ V32) {
+                              double* __restrict__ V64, float* __restrict__ V32, float2* __restrict__ V2) {
   long long tot = (long long)ncol * ld;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
     int row = (int)(id / ld), i = (int)(id % ld);
     double v = i < r ? VT[(long long)row * ncol + keep[i]] : 0.0;
     V64[id] = v;
     V32[id] = (float)v;
+    V2[id] = split2(v);
   }
 }
 
@@ -83,7 +93,9 @@ struct mfs_ctx {
   bool prof = false;
   mfs_timing_t tm{};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_pool;
-  long long pairs_per_apply = 0;
+  long long pairs_per_apply = 0, proxy_per_apply = 0, image_per_apply = 0;
+  long long build_id = 0;
+  struct BatchPlan* batch = nullptr;  // cached lockstep-batch workspace (owned when this is the first context)
   double gemv_bytes32 = 0, gemv_bytes64 = 0;
   int P = 0;
   double a = 1.0;
@@ -108,6 +120,7 @@ struct mfs_ctx {
   double *d_v = nullptr, *d_om = nullptr, *d_wb = nullptr, *d_mu = nullptr, *d_r = nullptr, *d_w64 = nullptr;
   double *d_tmp64 = nullptr, *d_lh64 = nullptr, *d_lam = nullptr, *d_F = nullptr, *d_T = nullptr;
   float *d_tmp32 = nullptr, *d_lh32 = nullptr, *d_in32 = nullptr, *d_out32 = nullptr, *d_mu32 = nullptr;
+  float2 *d_x2 = nullptr, *d_t2 = nullptr;  // double-float staging of step 1
   // Krylov workspace (lazily sized)
   void* d_basis = nullptr;
   size_t basis_bytes = 0;
@@ -225,10 +238,19 @@ void collect_events(mfs_ctx* c) {
   cudaGetLastError();
 }
 
-// step 1: lambda_hat = B^+ mu (two factors in turn, eq. transform)
+// step 1: lambda_hat = B^+ mu (two factors in turn, eq. transform); in the mixed mode the FP64
+// factors are applied in double-float arithmetic from their (hi, lo) float copies
 template <typename T>
 void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
   timed(c, c->ev_gemv, [&] {
+    if constexpr (sizeof(T) == 8) {
+      if (c->dw_pairs) {
+        launch_split_dw(c->n, mu, c->d_x2, c->stream);
+        launch_gemv_dw(Ops<T>::A(c), c->d_x2, c->d_t2, nullptr, c->stream);
+        launch_gemv_dw(Ops<T>::V(c), c->d_t2, nullptr, lam_hat, c->stream);
+        return;
+      }
+    }
     launch_gemv<T>(Ops<T>::A(c), mu, Ops<T>::tmp(c), c->stream);
     launch_gemv<T>(Ops<T>::V(c), Ops<T>::tmp(c), lam_hat, c->stream);
   });
@@ -250,6 +272,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
   });
   c->tm.pair_launches += 1;
   c->tm.pair_interactions += c->pairs_per_apply;
+  c->tm.pair_proxy += c->proxy_per_apply;
+  c->tm.pair_image_nodes += c->image_per_apply;
   c->tm.pair_kind = sizeof(T) == 4 ? MFS_FP32 : (c->dw_pairs ? MFS_MIXED : MFS_FP64);
 }
 
@@ -416,6 +440,517 @@ mfs_status check_state(mfs_ctx* c, int need) {
 
 }  // namespace
 
+// ================================================================== lockstep batch of problems
+struct BatchPlan {
+  std::vector<mfs_ctx*> key;
+  std::vector<long long> key_build;
+  int K = 0, nt = 1;
+  long long n_total = 0, u_total = 0, t_total = 0;
+  std::vector<long long> voff, uoff, toff;
+  std::vector<long long> pairs_p, proxy_p, image_p;
+  std::vector<void*> allocs;
+  void* d_args = nullptr;
+  int2* d_work = nullptr;
+  int n_work = 0;
+  int* d_active = nullptr;
+  long long *d_uoff = nullptr, *d_voff = nullptr;
+  GemvBatch<double> gA, gV;
+  SegTable seg;
+  double *wb = nullptr, *x = nullptr, *r = nullptr, *e = nullptr, *w = nullptr, *lh = nullptr, *tmp = nullptr,
+         *lam = nullptr, *partial = nullptr, *hbuf = nullptr, *coef = nullptr, *scl = nullptr;
+  float2 *x2 = nullptr, *t2 = nullptr;
+  double* basis = nullptr;
+  size_t basis_cap = 0;
+  double* hpin = nullptr;  // pinned host staging for the Arnoldi coefficients
+  int* apin = nullptr;     // pinned host staging for the active flags
+  cudaEvent_t ev = nullptr;
+  ~BatchPlan() {
+    for (void* q : allocs) cudaFree(q);
+    if (basis) cudaFree(basis);
+    if (hpin) cudaFreeHost(hpin);
+    if (apin) cudaFreeHost(apin);
+    if (ev) cudaEventDestroy(ev);
+  }
+  template <typename T>
+  T* alloc(size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    allocs.push_back(q);
+    return static_cast<T*>(q);
+  }
+};
+
+namespace {
+
+constexpr int kMaxBatchVec = 512;  // restart + 1 must fit the segmented update's coefficient cache
+
+template <typename T>
+bool put(BatchPlan* B, T*& dst, const std::vector<T>& v) {
+  dst = B->alloc<T>(v.size());
+  return dst && cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Builds the concatenated layout, the pair work list, the GEMV job tables and the vector chunks.
+mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) {
+  BatchPlan* B = new (std::nothrow) BatchPlan();
+  if (!B) return c0->fail(MFS_ERR_OOM, "host allocation failed: batch plan");
+  B->K = K;
+  B->key.assign(ctxs, ctxs + K);
+  for (int p = 0; p < K; ++p) B->key_build.push_back(ctxs[p]->build_id);
+  B->voff.assign(K + 1, 0);
+  B->uoff.assign(K + 1, 0);
+  B->toff.assign(K + 1, 0);
+  long long tiles_large = 0;
+  for (int p = 0; p < K; ++p) {
+    mfs_ctx* c = ctxs[p];
+    B->voff[p + 1] = B->voff[p] + c->n;
+    B->uoff[p + 1] = B->uoff[p] + c->n_unk;
+    B->toff[p + 1] = B->toff[p] + c->tmp_len;
+    B->pairs_p.push_back(c->pairs_per_apply);
+    B->proxy_p.push_back(c->proxy_per_apply);
+    B->image_p.push_back(c->image_per_apply);
+    tiles_large += c->tg.n_tiles;
+  }
+  B->n_total = B->voff[K];
+  B->u_total = B->uoff[K];
+  B->t_total = B->toff[K];
+  B->nt = pair_nodes_per_thread((int)std::min<long long>(tiles_large, 1 << 30));
+  // pair kernel arguments and work list
+  const size_t asz = pair_args64_bytes();
+  std::vector<char> args(asz * K);
+  std::vector<int2> work;
+  for (int p = 0; p < K; ++p) {
+    mfs_ctx* c = ctxs[p];
+    fill_pair_args64(args.data() + asz * p, c->tg, c->src, nullptr, nullptr, nullptr, c->hd.prm.visc, B->nt);
+    int nt_tiles = B->nt == 4 ? c->tg.n_tiles : c->tg.n_tiles1;
+    for (int t = 0; t < nt_tiles; ++t) work.push_back(make_int2(p, t));
+  }
+  B->n_work = (int)work.size();
+  B->d_args = B->alloc<char>(args.size());
+  bool ok = B->d_args && cudaMemcpy(B->d_args, args.data(), args.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && put(B, B->d_work, work) && put(B, B->d_uoff, B->uoff) && put(B, B->d_voff, B->voff);
+  B->d_active = B->alloc<int>(K);
+  ok = ok && B->d_active;
+  // GEMV jobs: every sphere of every problem
+  std::vector<const double*> mA, mV;
+  std::vector<const float2*> mA2, mV2;
+  std::vector<int> rA, cA, lA, rV, cV, lV, jp;
+  std::vector<long long> xA, yA, xV, yV;
+  int maxA = 0, maxV = 0;
+  for (int p = 0; p < K && ok; ++p) {
+    mfs_ctx* c = ctxs[p];
+    const HostDisc& d = c->hd;
+    long long toff = 0;
+    for (int k = 0; k < d.P; ++k) {
+      const Factor& F = c->factors[d.factor_id[k]];
+      mA.push_back(F.A64);
+      mV.push_back(F.V64);
+      mA2.push_back(F.A2);
+      mV2.push_back(F.V2);
+      rA.push_back(F.rank); cA.push_back(F.m); lA.push_back(F.ldA);
+      xA.push_back(B->voff[p] + 3LL * d.colloc_off[k]);
+      yA.push_back(B->toff[p] + toff);
+      rV.push_back(F.ncol); cV.push_back(F.rank); lV.push_back(F.ldV);
+      xV.push_back(B->toff[p] + toff);
+      yV.push_back(B->uoff[p] + d.unk_off[k]);
+      jp.push_back(p);
+      toff += F.rank;
+      maxA = std::max(maxA, F.rank);
+      maxV = std::max(maxV, F.ncol);
+    }
+  }
+  const double** dmA = nullptr;
+  const double** dmV = nullptr;
+  const float2** dmA2 = nullptr;
+  const float2** dmV2 = nullptr;
+  int *drA, *dcA, *dlA, *drV, *dcV, *dlV, *djp;
+  long long *dxA, *dyA, *dxV, *dyV;
+  ok = ok && put(B, dmA, mA) && put(B, dmV, mV) && put(B, drA, rA) && put(B, dcA, cA) && put(B, dlA, lA) &&
+       put(B, drV, rV) && put(B, dcV, cV) && put(B, dlV, lV) && put(B, djp, jp) && put(B, dxA, xA) &&
+       put(B, dyA, yA) && put(B, dxV, xV) && put(B, dyV, yV) && put(B, dmA2, mA2) && put(B, dmV2, mV2);
+  if (ok) {
+    B->gA.mat_dw = dmA2;
+    B->gV.mat_dw = dmV2;
+    B->gA.mat = dmA; B->gA.rows = drA; B->gA.cols = dcA; B->gA.ld = dlA; B->gA.x_off = dxA; B->gA.y_off = dyA;
+    B->gA.n_jobs = (int)mA.size(); B->gA.max_rows = maxA; B->gA.job_prob = djp; B->gA.active = B->d_active;
+    B->gV.mat = dmV; B->gV.rows = drV; B->gV.cols = dcV; B->gV.ld = dlV; B->gV.x_off = dxV; B->gV.y_off = dyV;
+    B->gV.n_jobs = (int)mV.size(); B->gV.max_rows = maxV; B->gV.job_prob = djp; B->gV.active = B->d_active;
+  }
+  // vector chunks, each inside one problem
+  const long long chunk = 4096;
+  std::vector<int> cprob, pchunk(1, 0);
+  std::vector<long long> cs, ce;
+  for (int p = 0; p < K; ++p) {
+    for (long long a = B->voff[p]; a < B->voff[p + 1]; a += chunk) {
+      cprob.push_back(p);
+      cs.push_back(a);
+      ce.push_back(std::min(B->voff[p + 1], a + chunk));
+    }
+    pchunk.push_back((int)cprob.size());
+  }
+  int *dcp = nullptr, *dpc = nullptr;
+  long long *dcs = nullptr, *dce = nullptr;
+  ok = ok && put(B, dcp, cprob) && put(B, dpc, pchunk) && put(B, dcs, cs) && put(B, dce, ce);
+  if (ok) {
+    B->seg.K = K;
+    B->seg.nchunks = (int)cprob.size();
+    B->seg.prob = dcp;
+    B->seg.start = dcs;
+    B->seg.end = dce;
+    B->seg.pchunk = dpc;
+    B->seg.active = B->d_active;
+  }
+  const long long n = B->n_total;
+  ok = ok && (B->wb = B->alloc<double>(n)) && (B->x = B->alloc<double>(n)) && (B->r = B->alloc<double>(n)) &&
+       (B->e = B->alloc<double>(n)) && (B->w = B->alloc<double>(n)) && (B->lh = B->alloc<double>(B->u_total)) &&
+       (B->tmp = B->alloc<double>(B->t_total)) && (B->lam = B->alloc<double>(B->u_total)) &&
+       (B->partial = B->alloc<double>((size_t)kMaxBatchVec * B->seg.nchunks)) &&
+       (B->hbuf = B->alloc<double>((size_t)(2 * kMaxBatchVec + 1) * K)) &&
+       (B->coef = B->alloc<double>((size_t)kMaxBatchVec * K)) && (B->scl = B->alloc<double>(K)) &&
+       (B->x2 = B->alloc<float2>(n)) && (B->t2 = B->alloc<float2>(B->t_total));
+  ok = ok && cudaMallocHost(&B->hpin, sizeof(double) * (2 * kMaxBatchVec + 1) * K) == cudaSuccess &&
+       cudaMallocHost(&B->apin, sizeof(int) * K) == cudaSuccess && cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    delete B;
+    return c0->fail(MFS_ERR_OOM, "device allocation failed: batch plan");
+  }
+  out = B;
+  return MFS_OK;
+}
+
+struct BatchRun {
+  mfs_ctx* c0;
+  BatchPlan* B;
+  cudaStream_t st;
+  bool dw;
+  std::vector<int> act;  // host copy of the active flags
+};
+
+mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
+  R.act = a;
+  for (int p = 0; p < R.B->K; ++p) R.B->apin[p] = a[p];
+  CUDA_TRY(R.c0, cudaMemcpyAsync(R.B->d_active, R.B->apin, sizeof(int) * R.B->K, cudaMemcpyHostToDevice, R.st));
+  // the pinned staging buffer is rewritten by the next call: wait for this copy
+  CUDA_TRY(R.c0, cudaStreamSynchronize(R.st));
+  return MFS_OK;
+}
+
+// out = G_hat in for every active problem
+void batch_apply(BatchRun& R, const double* in, double* out) {
+  mfs_ctx* c = R.c0;
+  BatchPlan* B = R.B;
+  timed(c, c->ev_gemv, [&] {
+    if (R.dw) {
+      launch_split_dw(B->n_total, in, B->x2, R.st);
+      launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
+      launch_gemv_dw(B->gV, B->t2, nullptr, B->lh, R.st);
+    } else {
+      launch_gemv<double>(B->gA, in, B->tmp, R.st);
+      launch_gemv<double>(B->gV, B->tmp, B->lh, R.st);
+    }
+  });
+  timed(c, c->ev_pair, [&] {
+    launch_pairs_batch64(R.dw, B->d_args, B->d_work, B->n_work, B->d_active, B->nt, B->lh, in, out, B->d_uoff,
+                         B->d_voff, R.st);
+  });
+  c->tm.gemv_launches += 2;
+  c->tm.pair_launches += 1;
+  c->tm.pair_kind = R.dw ? MFS_MIXED : MFS_FP64;
+  for (int p = 0; p < B->K; ++p)
+    if (R.act[p]) {
+      c->tm.pair_interactions += B->pairs_p[p];
+      c->tm.pair_proxy += B->proxy_p[p];
+      c->tm.pair_image_nodes += B->image_p[p];
+      c->tm.gemv_bytes += B->key[p]->gemv_bytes64;
+    }
+}
+
+// per-problem 2-norms of v (active problems; others 0)
+mfs_status batch_norms(BatchRun& R, const double* v, std::vector<double>& nrm) {
+  BatchPlan* B = R.B;
+  double* hn = B->hbuf + (size_t)2 * kMaxBatchVec * B->K;
+  launch_seg_dots(B->seg, 1, v, B->n_total, v, B->partial, hn, R.st);
+  CUDA_TRY(R.c0, cudaMemcpyAsync(B->hpin, hn, sizeof(double) * B->K, cudaMemcpyDeviceToHost, R.st));
+  CUDA_TRY(R.c0, cudaStreamSynchronize(R.st));
+  nrm.assign(B->K, 0.0);
+  for (int p = 0; p < B->K; ++p) nrm[p] = R.act[p] ? std::sqrt(std::max(0.0, B->hpin[p])) : 0.0;
+  return MFS_OK;
+}
+
+// One GMRES cycle (at most `restart` iterations) from x = 0 for the problems with solve[p] = 1.
+mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std::vector<int>& solve,
+                             const std::vector<double>& tol, int restart, int iter_budget, std::vector<int>& iters,
+                             std::vector<double>& est) {
+  BatchPlan* B = R.B;
+  mfs_ctx* c = R.c0;
+  const int K = B->K;
+  const long long n = B->n_total;
+  const int ldh = restart + 1;
+  mfs_status s;
+  size_t need = (size_t)(restart + 1) * (size_t)n;
+  if (B->basis_cap < need) {
+    if (B->basis) cudaFree(B->basis);
+    B->basis = nullptr;
+    B->basis_cap = 0;
+    if (cudaMalloc(&B->basis, need * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return c->fail(MFS_ERR_OOM, "device allocation failed: batched Krylov basis");
+    }
+    B->basis_cap = need;
+  }
+  double* V = B->basis;
+  CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * n, R.st));
+  if ((s = set_active(R, solve)) != MFS_OK) return s;
+  std::vector<double> bn;
+  if ((s = batch_norms(R, b, bn)) != MFS_OK) return s;
+  std::vector<int> act(solve);
+  for (int p = 0; p < K; ++p)
+    if (act[p] && !(bn[p] > 0)) {
+      if (!std::isfinite(bn[p])) return c->fail(MFS_ERR_NUMERIC, "right-hand side is not finite");
+      act[p] = 0;
+    }
+  if ((s = set_active(R, act)) != MFS_OK) return s;
+  const std::vector<int> started(act);
+  std::vector<double> sc(K, 0.0);
+  for (int p = 0; p < K; ++p) sc[p] = act[p] ? 1.0 / bn[p] : 0.0;
+  CUDA_TRY(c, cudaMemcpyAsync(B->scl, sc.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+  launch_seg_scale(B->seg, B->scl, b, V, R.st);
+  std::vector<std::vector<double>> H(K), cs(K), sn(K), g(K);
+  std::vector<int> jused(K, 0);
+  for (int p = 0; p < K; ++p)
+    if (act[p]) {
+      H[p].assign((size_t)ldh * restart, 0.0);
+      cs[p].assign(restart, 0.0);
+      sn[p].assign(restart, 0.0);
+      g[p].assign(ldh, 0.0);
+      g[p][0] = bn[p];
+      est[p] = 1.0;
+    }
+  double* h1 = B->hbuf;
+  double* h2 = B->hbuf + (size_t)kMaxBatchVec * K;
+  double* hn = B->hbuf + (size_t)2 * kMaxBatchVec * K;
+  int used = 0;
+  for (int j = 0; j < restart && used < iter_budget; ++j) {
+    bool any = false;
+    for (int p = 0; p < K; ++p) any = any || act[p];
+    if (!any) break;
+    double* w = V + (size_t)(j + 1) * n;
+    batch_apply(R, V + (size_t)j * n, w);
+    launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h1, R.st);
+    launch_seg_update(B->seg, j + 1, V, n, h1, -1.0, w, R.st);
+    launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h2, R.st);
+    launch_seg_update(B->seg, j + 1, V, n, h2, -1.0, w, R.st);
+    launch_seg_dots(B->seg, 1, w, n, w, B->partial, hn, R.st);
+    CHECK_LAUNCH(c);
+    double* hp = B->hpin;
+    CUDA_TRY(c, cudaMemcpyAsync(hp, h1, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, R.st));
+    CUDA_TRY(c, cudaMemcpyAsync(hp + (size_t)kMaxBatchVec * K, h2, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, R.st));
+    CUDA_TRY(c, cudaMemcpyAsync(hp + (size_t)2 * kMaxBatchVec * K, hn, sizeof(double) * K, cudaMemcpyDeviceToHost, R.st));
+    CUDA_TRY(c, cudaStreamSynchronize(R.st));
+    ++used;
+    std::vector<int> next(act);
+    for (int p = 0; p < K; ++p) {
+      if (!act[p]) continue;
+      double* col = &H[p][(size_t)j * ldh];
+      for (int i = 0; i <= j; ++i) col[i] = hp[(size_t)i * K + p] + hp[(size_t)kMaxBatchVec * K + (size_t)i * K + p];
+      const double hnext = std::sqrt(std::max(0.0, hp[(size_t)2 * kMaxBatchVec * K + p]));
+      if (!std::isfinite(hnext)) return c->fail(MFS_ERR_NUMERIC, "non-finite value in the batched Arnoldi process");
+      col[j + 1] = hnext;
+      for (int i = 0; i < j; ++i) {
+        double t = cs[p][i] * col[i] + sn[p][i] * col[i + 1];
+        col[i + 1] = -sn[p][i] * col[i] + cs[p][i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[p][j] = den > 0 ? col[j] / den : 1.0;
+      sn[p][j] = den > 0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[p][j + 1] = -sn[p][j] * g[p][j];
+      g[p][j] = cs[p][j] * g[p][j];
+      jused[p] = j + 1;
+      ++iters[p];
+      est[p] = std::fabs(g[p][j + 1]) / bn[p];
+      sc[p] = hnext > 0 ? 1.0 / hnext : 0.0;
+      if (est[p] <= tol[p] || hnext == 0.0) next[p] = 0;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(B->scl, sc.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+    launch_seg_scale(B->seg, B->scl, w, w, R.st);
+    act = next;
+    if ((s = set_active(R, act)) != MFS_OK) return s;
+  }
+  // x = V y per problem, y = R^{-1} g (zero beyond the problem's own iterations)
+  int jmax = 0;
+  for (int p = 0; p < K; ++p) jmax = std::max(jmax, jused[p]);
+  if (jmax == 0) return MFS_OK;
+  std::vector<double> cf((size_t)jmax * K, 0.0);
+  for (int p = 0; p < K; ++p) {
+    const int J = jused[p];
+    std::vector<double> y(J, 0.0);
+    for (int i = J - 1; i >= 0; --i) {
+      double t = g[p][i];
+      for (int q = i + 1; q < J; ++q) t -= H[p][(size_t)q * ldh + i] * y[q];
+      const double diag = H[p][(size_t)i * ldh + i];
+      y[i] = diag != 0.0 ? t / diag : 0.0;
+    }
+    for (int i = 0; i < J; ++i) cf[(size_t)i * K + p] = y[i];
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(B->coef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, R.st));
+  if ((s = set_active(R, started)) != MFS_OK) return s;
+  launch_seg_update(B->seg, jmax, V, n, B->coef, 1.0, x, R.st);
+  CHECK_LAUNCH(c);
+  return MFS_OK;
+}
+
+mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos) {
+  auto t0 = std::chrono::steady_clock::now();
+  mfs_ctx* c0 = ctxs[0];
+  for (int p = 0; p < K; ++p) {
+    mfs_status s = check_state(ctxs[p], 2);
+    if (s != MFS_OK) return s;
+    if (ctxs[p]->device != c0->device) return c0->fail(MFS_ERR_ARG, "batched contexts must share one device");
+    for (int q = 0; q < p; ++q)
+      if (ctxs[q] == ctxs[p]) return c0->fail(MFS_ERR_ARG, "a context appears twice in the batch");
+  }
+  if (o.restart < 1 || o.restart + 1 > kMaxBatchVec || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0)
+    return c0->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 511])");
+  check_state(c0, 2);
+  // reuse the cached plan when the same contexts with the same builds come back
+  BatchPlan* B = c0->batch;
+  bool same = B && B->K == K;
+  for (int p = 0; same && p < K; ++p) same = B->key[p] == ctxs[p] && B->key_build[p] == ctxs[p]->build_id;
+  if (!same) {
+    if (B) delete B;
+    c0->batch = nullptr;
+    mfs_status s = make_plan(c0, K, ctxs, B);
+    if (s != MFS_OK) return s;
+    c0->batch = B;
+  }
+  BatchRun R{c0, B, c0->stream, o.precision == MFS_MIXED, std::vector<int>(K, 1)};
+  // order after the work already queued on every context's stream
+  for (int p = 0; p < K; ++p)
+    if (ctxs[p]->stream != R.st) {
+      CUDA_TRY(c0, cudaEventRecord(B->ev, ctxs[p]->stream));
+      CUDA_TRY(c0, cudaStreamWaitEvent(R.st, B->ev, 0));
+    }
+  for (int p = 0; p < K; ++p) {
+    mfs_ctx* c = ctxs[p];
+    launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(),
+               B->wb + B->voff[p], R.st);
+  }
+  CHECK_LAUNCH(c0);
+  mfs_status s;
+  std::vector<int> all(K, 1);
+  if ((s = set_active(R, all)) != MFS_OK) return s;
+  std::vector<double> bnorm, rn;
+  if ((s = batch_norms(R, B->wb, bnorm)) != MFS_OK) return s;
+  const long long n = B->n_total;
+  CUDA_TRY(c0, cudaMemsetAsync(B->x, 0, sizeof(double) * n, R.st));
+  CUDA_TRY(c0, cudaMemcpyAsync(B->r, B->wb, sizeof(double) * n, cudaMemcpyDeviceToDevice, R.st));
+  std::vector<double> rel(K), est(K, 0.0);
+  std::vector<int> iters(K, 0), refines(K, 0), stalled(K, 0);
+  for (int p = 0; p < K; ++p) {
+    if (!std::isfinite(bnorm[p])) return ctxs[p]->fail(MFS_ERR_NUMERIC, "boundary data is not finite");
+    rel[p] = bnorm[p] > 0 ? 1.0 : 0.0;
+  }
+  const int max_outer = std::max(o.max_refine, o.max_iter / o.restart + 2);
+  int total_iters = 0;
+  for (int outer = 0; outer < max_outer; ++outer) {
+    std::vector<int> solve_p(K, 0);
+    std::vector<double> tol_p(K, 0.5);
+    bool any = false;
+    for (int p = 0; p < K; ++p) {
+      solve_p[p] = rel[p] > o.tol && !stalled[p];
+      tol_p[p] = solve_p[p] ? std::min(0.5, 0.5 * o.tol / rel[p]) : 0.5;
+      any = any || solve_p[p];
+    }
+    if (!any || total_iters >= o.max_iter) break;
+    std::vector<int> it_before(iters);
+    if ((s = batch_gmres_cycle(R, B->r, B->e, solve_p, tol_p, o.restart, o.max_iter - total_iters, iters, est)) != MFS_OK)
+      return s;
+    int cyc = 0;
+    for (int p = 0; p < K; ++p) cyc = std::max(cyc, iters[p] - it_before[p]);
+    total_iters += cyc;
+    launch_axpy64(n, 1.0, B->e, B->x, R.st);
+    // true residual of every problem with data
+    std::vector<int> live(K);
+    for (int p = 0; p < K; ++p) live[p] = bnorm[p] > 0;
+    if ((s = set_active(R, live)) != MFS_OK) return s;
+    batch_apply(R, B->x, B->w);
+    launch_sub((int)n, B->wb, B->w, B->r, R.st);
+    CHECK_LAUNCH(c0);
+    if ((s = batch_norms(R, B->r, rn)) != MFS_OK) return s;
+    for (int p = 0; p < K; ++p) {
+      if (!live[p]) continue;
+      double prev = rel[p];
+      rel[p] = rn[p] / bnorm[p];
+      if (!std::isfinite(rel[p])) return ctxs[p]->fail(MFS_ERR_NUMERIC, "residual is not finite");
+      if (solve_p[p]) {
+        if (outer > 0) ++refines[p];
+        if (rel[p] >= prev && rel[p] > o.tol) stalled[p] = 1;  // a pass that gained nothing
+      }
+    }
+  }
+  // lambda = B^+ mu, then per-context outputs
+  std::vector<int> live(K);
+  for (int p = 0; p < K; ++p) live[p] = 1;
+  if ((s = set_active(R, live)) != MFS_OK) return s;
+  timed(c0, c0->ev_gemv, [&] {
+    launch_gemv<double>(B->gA, B->x, B->tmp, R.st);
+    launch_gemv<double>(B->gV, B->tmp, B->lam, R.st);
+  });
+  for (int p = 0; p < K; ++p) {
+    mfs_ctx* c = ctxs[p];
+    CUDA_TRY(c0, cudaMemcpyAsync(c->d_mu, B->x + B->voff[p], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, R.st));
+    CUDA_TRY(c0, cudaMemcpyAsync(c->d_lam, B->lam + B->uoff[p], sizeof(double) * c->n_unk, cudaMemcpyDeviceToDevice, R.st));
+    launch_forces_torques(c->src, c->d_lam, c->d_F, c->d_T, R.st);
+  }
+  CHECK_LAUNCH(c0);
+  CUDA_TRY(c0, cudaEventRecord(B->ev, R.st));
+  for (int p = 0; p < K; ++p)
+    if (ctxs[p]->stream != R.st) CUDA_TRY(c0, cudaStreamWaitEvent(ctxs[p]->stream, B->ev, 0));
+  CUDA_TRY(c0, cudaStreamSynchronize(R.st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  mfs_status first = MFS_OK;
+  for (int p = 0; p < K; ++p) {
+    mfs_ctx* c = ctxs[p];
+    c->solved = true;
+    bool conv = rel[p] <= o.tol;
+    if (infos) {
+      infos[p].iters = iters[p];
+      infos[p].refinements = refines[p];
+      infos[p].rel_residual = rel[p];
+      infos[p].seconds = secs;
+      infos[p].converged = conv ? 1 : 0;
+    }
+    if (!conv) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "not converged: relative residual %.3e after %d iterations", rel[p], iters[p]);
+      c->fail(MFS_ERR_NOT_CONVERGED, buf);
+      if (first == MFS_OK) first = MFS_ERR_NOT_CONVERGED;
+    }
+  }
+  return first;
+}
+
+mfs_status batch_lockstep(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos) {
+  mfs_ctx* c0 = ctxs[0];
+  const long long l0 = launches_on_this_thread();
+  mfs_status s = batch_lockstep_impl(K, ctxs, o, infos);
+  c0->tm.kernel_launches += launches_on_this_thread() - l0;
+  if (c0->prof) {
+    cudaStreamSynchronize(c0->stream);
+    collect_events(c0);
+  }
+  return s;
+}
+
+}  // namespace
+
 // ================================================================== C ABI
 extern "C" {
 
@@ -478,6 +1013,8 @@ void mfs_destroy(mfs_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  delete c->batch;
+  c->batch = nullptr;
   c->free_build();
   for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_pool})
     for (auto& e : *lst) {
@@ -540,7 +1077,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   // ---- targets: positions relative to the owner centre, tiles inside one sphere
   std::vector<float4> t32(nc);
   std::vector<double> t64(4 * (size_t)nc), cabs(d.colloc), sw(nc);
-  std::vector<int> ts, tst, tcn;
+  std::vector<int> ts, tst, tcn, ts1, tst1, tcn1;
   for (int k = 0; k < P; ++k) {
     for (int i = d.colloc_off[k]; i < d.colloc_off[k + 1]; ++i) {
       double r[3];
@@ -555,7 +1092,16 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
       tst.push_back(s0);
       tcn.push_back(std::min(kTileTargets, d.colloc_off[k + 1] - s0));
     }
+    for (int s0 = d.colloc_off[k]; s0 < d.colloc_off[k + 1]; s0 += kTileTargets / 4) {
+      ts1.push_back(k);
+      tst1.push_back(s0);
+      tcn1.push_back(std::min(kTileTargets / 4, d.colloc_off[k + 1] - s0));
+    }
   }
+  c->tg.n_tiles1 = (int)ts1.size();
+  if ((s = upload(c, c->tg.tile1_sphere, ts1)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.tile1_start, tst1)) != MFS_OK) return s;
+  if ((s = upload(c, c->tg.tile1_count, tcn1)) != MFS_OK) return s;
   c->tg.n = nc;
   c->tg.n_tiles = (int)ts.size();
   if ((s = upload(c, c->tg.pos32, t32)) != MFS_OK) return s;
@@ -759,13 +1305,15 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
         F.A32 = c->dalloc<float>((size_t)r * F.ldA);
         F.V64 = c->dalloc<double>((size_t)ncol * F.ldV);
         F.V32 = c->dalloc<float>((size_t)ncol * F.ldV);
+        F.A2 = c->dalloc<float2>((size_t)r * F.ldA);
+        F.V2 = c->dalloc<float2>((size_t)ncol * F.ldV);
       }
-      if (!F.A64 || !F.A32 || !F.V64 || !F.V32) {
+      if (!F.A64 || !F.A32 || !F.V64 || !F.V32 || !F.A2 || !F.V2) {
         fail_w(MFS_ERR_OOM, "device allocation failed: one-body factors");
         break;
       }
-      pack_A_kernel<<<1024, 256, 0, st>>>(r, m, F.ldA, dU, dS, dkeep, F.A64, F.A32);
-      pack_V_kernel<<<1024, 256, 0, st>>>(ncol, r, F.ldV, dVT, dkeep, F.V64, F.V32);
+      pack_A_kernel<<<1024, 256, 0, st>>>(r, m, F.ldA, dU, dS, dkeep, F.A64, F.A32, F.A2);
+      pack_V_kernel<<<1024, 256, 0, st>>>(ncol, r, F.ldV, dVT, dkeep, F.V64, F.V32, F.V2);
       cudaError_t el = cudaGetLastError();
       if (el == cudaSuccess) el = cudaStreamSynchronize(st);  // keep and hS are reused next round
       if (el != cudaSuccess) {
@@ -790,12 +1338,14 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   {
     std::vector<const double*> mA64(P), mV64(P);
     std::vector<const float*> mA32(P), mV32(P);
+    std::vector<const float2*> mA2(P), mV2(P);
     std::vector<int> rA(P), cA(P), lA(P), rV(P), cV(P), lV(P);
     std::vector<long long> xA(P), yA(P), xV(P), yV(P);
     int maxA = 0, maxV = 0;
     for (int k = 0; k < P; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
       mA64[k] = F.A64; mA32[k] = F.A32; mV64[k] = F.V64; mV32[k] = F.V32;
+      mA2[k] = F.A2; mV2[k] = F.V2;
       rA[k] = F.rank; cA[k] = F.m; lA[k] = F.ldA;
       xA[k] = 3LL * d.colloc_off[k]; yA[k] = tmp_off[k];
       rV[k] = F.ncol; cV[k] = F.rank; lV[k] = F.ldV;
@@ -813,6 +1363,11 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
     c->gV64.mat = dm64;
     if ((s = upload(c, dm32, mV32)) != MFS_OK) return s;
     c->gV32.mat = dm32;
+    const float2** dm2 = nullptr;
+    if ((s = upload(c, dm2, mA2)) != MFS_OK) return s;
+    c->gA64.mat_dw = dm2;
+    if ((s = upload(c, dm2, mV2)) != MFS_OK) return s;
+    c->gV64.mat_dw = dm2;
     int *d_rA, *d_cA, *d_lA, *d_rV, *d_cV, *d_lV;
     long long *d_xA, *d_yA, *d_xV, *d_yV;
     if ((s = upload(c, d_rA, rA)) || (s = upload(c, d_cA, cA)) || (s = upload(c, d_lA, lA)) || (s = upload(c, d_rV, rV)) ||
@@ -853,6 +1408,8 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   ALLOC_TRY(c, c->d_in32, float, std::max<long long>(n, c->n_unk));
   ALLOC_TRY(c, c->d_out32, float, std::max<long long>(n, c->n_unk));
   ALLOC_TRY(c, c->d_mu32, float, n);
+  ALLOC_TRY(c, c->d_x2, float2, n);
+  ALLOC_TRY(c, c->d_t2, float2, c->tmp_len);
   c->nblk = std::max(1, std::min(1024, (n + 4095) / 4096));
   ALLOC_TRY(c, c->d_partial, double, (size_t)c->nblk * 512);
   ALLOC_TRY(c, c->d_h, double, 5 * 512);
@@ -864,6 +1421,16 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
     c->state = 2;
     mfs_sizes(c, &sz);
     c->pairs_per_apply = sz.pairs_fp;
+    long long pp = 0, ip = 0;
+    for (int k = 0; k < P; ++k) {
+      long long mk = d.colloc_off[k + 1] - d.colloc_off[k];
+      pp += mk * (long long)(P - 1) * N;
+      ip += mk * (long long)(ni - (d.img_off[k + 1] - d.img_off[k]));
+    }
+    c->proxy_per_apply = pp;
+    c->image_per_apply = ip;
+    static std::atomic<long long> g_build_counter{0};
+    c->build_id = ++g_build_counter;
     double b32 = 0, b64 = 0;
     for (int k = 0; k < P; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
@@ -1225,12 +1792,17 @@ mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve
   if (n_problems < 0 || (n_problems > 0 && !ctxs)) return MFS_ERR_ARG;
   for (int i = 0; i < n_problems; ++i)
     if (!ctxs[i]) return MFS_ERR_ARG;
+  if (n_problems == 0) return MFS_OK;
+  mfs_solve_opts o;
+  if (opts) o = *opts; else mfs_default_solve_opts(&o);
+  if (o.precision == MFS_FP64 || o.precision == MFS_MIXED) return batch_lockstep(n_problems, ctxs, o, infos);
+  // MFS_FP32: independent solves, concurrently on the contexts' own streams
   std::vector<mfs_status> st(n_problems, MFS_OK);
   std::atomic<int> next{0};
   unsigned hw = std::thread::hardware_concurrency();
   int n_threads = std::max(1, std::min(n_problems, (int)std::max(4u, std::min(hw ? 2 * hw : 16u, 64u))));
   auto work = [&]() {
-    for (int i = next++; i < n_problems; i = next++) st[i] = mfs_solve(ctxs[i], opts, infos ? &infos[i] : nullptr);
+    for (int i = next++; i < n_problems; i = next++) st[i] = mfs_solve(ctxs[i], &o, infos ? &infos[i] : nullptr);
   };
   std::vector<std::thread> pool;
   for (int t = 0; t < n_threads; ++t) pool.emplace_back(work);

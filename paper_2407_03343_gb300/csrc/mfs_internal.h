@@ -53,13 +53,20 @@ mfs_status build_discretisation(const double* centres, int P, double a, const mf
 // a sphere, so the self block of step 2 can be skipped per tile (Sec. 2.2, direct summation).
 struct TargetSet {
   int n = 0;             // nodes
-  int n_tiles = 0;
+  int n_tiles = 0;       // tiles of up to 512 nodes (4 per thread)
+  int n_tiles1 = 0;      // tiles of up to 128 nodes (1 per thread), used when there are few large tiles
   float4* pos32 = nullptr;   // (x - c_k, y - c_k, z - c_k, sqrt w) per node, FP32
   double* pos64 = nullptr;   // same, 4 doubles per node
   int* tile_sphere = nullptr;
   int* tile_start = nullptr;
   int* tile_count = nullptr;
+  int* tile1_sphere = nullptr;
+  int* tile1_start = nullptr;
+  int* tile1_count = nullptr;
 };
+
+// Tile size choice: 4 nodes per thread once the large tiles fill the GPU twice over.
+inline int pair_nodes_per_thread(int n_tiles_large) { return n_tiles_large >= 2 * 152 ? 4 : 1; }
 
 struct SourceSet {
   int P = 0, N = 0, n_img = 0;
@@ -88,6 +95,15 @@ void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, c
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu,
                      double* out, double visc, cudaStream_t st);
 
+// Many problems per launch (FP64 data): a device table of per-problem kernel arguments, a work
+// list of (problem, tile) pairs and a per-problem active flag.
+size_t pair_args64_bytes();
+void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src, const double* lam_hat,
+                      const double* mu, double* out, double visc, int nodes_per_thread);
+void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
+                          int nodes_per_thread, const double* lam, const double* mu, double* out,
+                          const long long* d_uoff, const long long* d_voff, cudaStream_t st);
+
 // Batched GEMV: for every job j, y_j = M_j x_j with M_j row-major (rows_j x cols_j, leading dim ld_j).
 template <typename T>
 struct GemvBatch {
@@ -99,9 +115,17 @@ struct GemvBatch {
   long long* y_off = nullptr;
   int n_jobs = 0;
   int max_rows = 0;
+  const int* job_prob = nullptr;  // optional: problem of each job, with
+  const int* active = nullptr;    //   per-problem flags (jobs of inactive problems are skipped)
+  const float2** mat_dw = nullptr;  // optional: the same matrices as (hi, lo) float pairs
 };
 template <typename T>
 void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st);
+// Double-float GEMV on the FP32 pipes over b.mat_dw: x as (hi, lo) pairs; the result goes to
+// y_dw as pairs, or to y64 joined into doubles when y_dw is null.
+void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, double* y64, cudaStream_t st);
+// (hi, lo) float pairs of a double vector.
+void launch_split_dw(long long n, const double* in, float2* out, cudaStream_t st);
 
 // Self block B_k = W_k G^(kk) assembled column-major FP64 (rows 3 M_k, cols 3 N_k, lda rows)
 // with columns in the strength order of the library.
@@ -123,6 +147,24 @@ template <typename Tin, typename Tout>
 void launch_convert(long long n, const Tin* in, double s, Tout* out, cudaStream_t st);
 void launch_axpy_mixed(int n, double a, const float* x, double* y, cudaStream_t st);
 void launch_sub(int n, const double* a, const double* b, double* out, cudaStream_t st);
+
+// Segmented vector kernels over a concatenation of independent problems: chunk b covers
+// [start[b], end[b]) and belongs to problem prob[b]; per-problem coefficients are stored
+// vector-major, c[i * K + p].  Chunks of inactive problems do nothing.
+struct SegTable {
+  int K = 0, nchunks = 0;
+  const int* prob = nullptr;
+  const long long* start = nullptr;
+  const long long* end = nullptr;
+  const int* pchunk = nullptr;  // K+1 chunk offsets per problem
+  const int* active = nullptr;
+};
+void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
+                     double* h, cudaStream_t st);
+void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
+                       double* w, cudaStream_t st);
+void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st);
+void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st);
 
 // Forces and torques (Sec. 2.3 remark), FP64, one CTA per sphere.
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st);

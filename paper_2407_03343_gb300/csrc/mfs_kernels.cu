@@ -21,6 +21,7 @@
 //  assemble_self       B_k = W_k G^(kk) column-major FP64 for the one-time factorisation.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "mfs_internal.h"
 
@@ -28,7 +29,6 @@ namespace mfs {
 namespace {
 
 constexpr int kPairThreads = 128;
-constexpr int kNT = 4;          // target nodes per thread
 constexpr int kTileProxy = 256; // proxy sources staged per round
 constexpr int kTileImg = 128;   // image nodes staged per round
 constexpr double kPi = 3.14159265358979323846;
@@ -114,14 +114,14 @@ struct PairArgs {
   T dip;         // 2 mu: dipole strengths rescaled so that scale * dip = 1 / (4 pi)
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
+// One target tile (NT nodes per thread) against every source of every other sphere.
+template <typename T, int NT>
+__device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
   using V4 = typename Prec<T>::V4;
   __shared__ V4 sp[kTileProxy];
   __shared__ V4 sf[kTileProxy];
   __shared__ V4 si[3 * kTileImg];
 
-  const int t = blockIdx.x;
   const int k = A.tile_sphere[t];
   const int start = A.tile_start[t];
   const int cnt = A.tile_count[t];
@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
   if constexpr (sizeof(T) == 4) { sh.hi = A.cen_hi; sh.lo = A.cen_lo; } else { sh.cen = A.cen64; }
   sh.init(k);
 
-  T x[kNT], y[kNT], z[kNT], ux[kNT], uy[kNT], uz[kNT];
-  T sx[kNT], sy[kNT], sz[kNT], cx[kNT], cy[kNT], cz[kNT];
+  T x[NT], y[NT], z[NT], ux[NT], uy[NT], uz[NT];
+  T sx[NT], sy[NT], sz[NT], cx[NT], cy[NT], cz[NT];
 #pragma unroll
-  for (int q = 0; q < kNT; ++q) {
+  for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     int node = start + (idx < cnt ? idx : cnt - 1);
     V4 p = A.tgt[node];
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
       const V4 p = sp[j];
       const V4 f = sf[j];
 #pragma unroll
-      for (int q = 0; q < kNT; ++q) {
+      for (int q = 0; q < NT; ++q) {
         T dx = x[q] - p.x, dy = y[q] - p.y, dz = z[q] - p.z;
         T r2 = dx * dx + dy * dy + dz * dz;
         T ir = Prec<T>::rsq(r2);
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
       }
     }
 #pragma unroll
-    for (int q = 0; q < kNT; ++q) {
+    for (int q = 0; q < NT; ++q) {
       comp_add(sx[q], cx[q], ux[q]);
       comp_add(sy[q], cy[q], uy[q]);
       comp_add(sz[q], cz[q], uz[q]);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
       const V4 a = si[3 * j], b = si[3 * j + 1], c = si[3 * j + 2];
       // f = (a.w, b.x, b.y), t = (b.z, b.w, c.x), d = (c.y, c.z, c.w)
 #pragma unroll
-      for (int q = 0; q < kNT; ++q) {
+      for (int q = 0; q < NT; ++q) {
         T dx = x[q] - a.x, dy = y[q] - a.y, dz = z[q] - a.z;
         T r2 = dx * dx + dy * dy + dz * dz;
         T ir = Prec<T>::rsq(r2);
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
       }
     }
 #pragma unroll
-    for (int q = 0; q < kNT; ++q) {
+    for (int q = 0; q < NT; ++q) {
       comp_add(sx[q], cx[q], ux[q]);
       comp_add(sy[q], cy[q], uy[q]);
       comp_add(sz[q], cz[q], uz[q]);
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
   }
 
 #pragma unroll
-  for (int q = 0; q < kNT; ++q) {
+  for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     if (idx < cnt) {
       long long node = start + idx;
@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
 }
 
 template <typename T>
-PairArgs<T> make_args(const TargetSet& tg, const SourceSet& src, const T* lam, const T* mu, T* out, double visc) {
+PairArgs<T> make_args(const TargetSet& tg, const SourceSet& src, const T* lam, const T* mu, T* out, double visc,
+                      int nt = 4) {
   PairArgs<T> A;
   if constexpr (sizeof(T) == 4) {
     A.tgt = tg.pos32;
@@ -287,9 +288,9 @@ PairArgs<T> make_args(const TargetSet& tg, const SourceSet& src, const T* lam, c
     A.proxy = reinterpret_cast<const D4*>(src.proxy64);
     A.img = reinterpret_cast<const D4*>(src.img64);
   }
-  A.tile_sphere = tg.tile_sphere;
-  A.tile_start = tg.tile_start;
-  A.tile_count = tg.tile_count;
+  A.tile_sphere = nt == 4 ? tg.tile_sphere : tg.tile1_sphere;
+  A.tile_start = nt == 4 ? tg.tile_start : tg.tile1_start;
+  A.tile_count = nt == 4 ? tg.tile_count : tg.tile1_count;
   A.N = src.N;
   A.P = src.P;
   A.img_owner = src.img_owner;
@@ -373,12 +374,12 @@ struct __align__(16) DWPos {
   float xl, yl, zl, pad1;
 };
 
-__global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A) {
+template <int NT>
+__device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const int t) {
   __shared__ float4 sp[2 * kTileProxy];   // position hi, lo
   __shared__ float4 sf[2 * kTileProxy];   // strength hi, lo
   __shared__ float4 si[6 * kTileImg];     // image node: 12 hi values (3 float4), then 12 lo values (3 float4)
 
-  const int t = blockIdx.x;
   const int k = A.tile_sphere[t];
   const int start = A.tile_start[t];
   const int cnt = A.tile_count[t];
@@ -386,9 +387,9 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
   sh.cen = A.cen64;
   sh.init(k);
 
-  dw x[kNT], y[kNT], z[kNT], ux[kNT], uy[kNT], uz[kNT];
+  dw x[NT], y[NT], z[NT], ux[NT], uy[NT], uz[NT];
 #pragma unroll
-  for (int q = 0; q < kNT; ++q) {
+  for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     int node = start + (idx < cnt ? idx : cnt - 1);
     D4 p = A.tgt[node];
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
       const float4 fh = sf[2 * j], fl = sf[2 * j + 1];
       const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
 #pragma unroll
-      for (int q = 0; q < kNT; ++q) {
+      for (int q = 0; q < NT; ++q) {
         dw dx = dw_sub(x[q], dw{ph.x, pl.x});
         dw dy = dw_sub(y[q], dw{ph.y, pl.y});
         dw dz = dw_sub(z[q], dw{ph.z, pl.z});
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
       const dw tx{h1.z, l1.z}, ty{h1.w, l1.w}, tz{h2.x, l2.x};
       const dw qx{h2.y, l2.y}, qy{h2.z, l2.z}, qz{h2.w, l2.w};
 #pragma unroll
-      for (int q = 0; q < kNT; ++q) {
+      for (int q = 0; q < NT; ++q) {
         dw dx = dw_sub(x[q], px), dy = dw_sub(y[q], py), dz = dw_sub(z[q], pz);
         dw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
         dw ir = dw_rsqrt(r2);
@@ -520,7 +521,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
   }
 
 #pragma unroll
-  for (int q = 0; q < kNT; ++q) {
+  for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     if (idx < cnt) {
       long long node = start + idx;
@@ -537,6 +538,49 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
       }
     }
   }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
+  pair_tile<T, NT>(A, blockIdx.x);
+}
+template <int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A) {
+  pair_tile_dw<NT>(A, blockIdx.x);
+}
+// Many problems in one launch: work[b] = (problem, tile); problems whose flag is 0 are skipped.
+// The per-problem vectors are segments of concatenated ones: lam at lam + uoff[p], mu and out
+// at mu + voff[p], out + voff[p].
+struct BatchVecs {
+  const double* lam;
+  const double* mu;
+  double* out;
+  const long long* uoff;
+  const long long* voff;
+};
+template <typename T, int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArgs<T>* __restrict__ args,
+                                                                   const int2* __restrict__ work,
+                                                                   const int* __restrict__ active, BatchVecs bv) {
+  const int2 w = work[blockIdx.x];
+  if (!active[w.x]) return;
+  PairArgs<T> A = args[w.x];
+  A.lam = bv.lam + bv.uoff[w.x];
+  A.mu = bv.mu + bv.voff[w.x];
+  A.out = bv.out + bv.voff[w.x];
+  pair_tile<T, NT>(A, w.y);
+}
+template <int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const PairArgs<double>* __restrict__ args,
+                                                                      const int2* __restrict__ work,
+                                                                      const int* __restrict__ active, BatchVecs bv) {
+  const int2 w = work[blockIdx.x];
+  if (!active[w.x]) return;
+  PairArgs<double> A = args[w.x];
+  A.lam = bv.lam + bv.uoff[w.x];
+  A.mu = bv.mu + bv.voff[w.x];
+  A.out = bv.out + bv.voff[w.x];
+  pair_tile_dw<NT>(A, w.y);
 }
 
 // ------------------------------------------------------------------ batched GEMV
@@ -561,6 +605,7 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, cons
   using VT = typename Vec<T>::type;
   constexpr int W = Vec<T>::w;
   const int job = blockIdx.y;
+  if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = (blockIdx.x * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
@@ -593,6 +638,69 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, cons
     T s = acc[r];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0 && r0 + r < nr) y[B.y_off[job] + r0 + r] = s;
+  }
+}
+
+// Double-float GEMV: each matrix element and each x element is a (hi, lo) float pair; products
+// and sums use the error-free double-word operations above, so the result carries ~2^-46
+// relative accuracy while reading the same 8 bytes per element as FP64.
+template <bool OUT64>
+__global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double> B, const float2* __restrict__ x,
+                                                                float2* __restrict__ y2, double* __restrict__ y64) {
+  const int job = blockIdx.y;
+  if (B.active && !B.active[B.job_prob[job]]) return;
+  const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = (blockIdx.x * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
+  if (r0 >= nr) return;
+  const float2* M = B.mat_dw[job];
+  const float2* xv = x + B.x_off[job];
+  dw acc[kGemvRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) acc[r] = dw{0.f, 0.f};
+  const int npair = nc / 2;  // two elements per 16-byte load
+  for (int v = lane; v < npair; v += 32) {
+    const float2 xa = xv[2 * v], xb = xv[2 * v + 1];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) {
+        float4 m = reinterpret_cast<const float4*>(M + (long long)row * ld)[v];
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.x, m.y}, dw{xa.x, xa.y}));
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.z, m.w}, dw{xb.x, xb.y}));
+      }
+    }
+  }
+  for (int cidx = 2 * npair + lane; cidx < nc; cidx += 32) {
+    const float2 xa = xv[cidx];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) {
+        float2 m = M[(long long)row * ld + cidx];
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.x, m.y}, dw{xa.x, xa.y}));
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+    dw s = acc[r];
+    for (int o = 16; o > 0; o >>= 1) {
+      dw t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
+      s = dw_add(s, t);
+    }
+    if (lane == 0 && r0 + r < nr) {
+      long long idx = B.y_off[job] + r0 + r;
+      if (OUT64) y64[idx] = dw_join(s);
+      else y2[idx] = make_float2(s.h, s.l);
+    }
+  }
+}
+
+__global__ void split_dw_kernel(long long n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    dw s = dw_split(in[e]);
+    out[e] = make_float2(s.h, s.l);
   }
 }
 
@@ -669,6 +777,88 @@ __global__ void axpy_mixed_kernel(int n, double a, const float* __restrict__ x, 
 __global__ void sub_kernel(int n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     out[e] = a[e] - b[e];
+}
+
+// ------------------------------------------------------------------ segmented (batched) vector kernels
+constexpr int kSegThreads = 256;
+
+__global__ void seg_dots_kernel(SegTable t, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+                                double* __restrict__ partial) {
+  const int b = blockIdx.x, i = blockIdx.y;
+  double d = 0.0;
+  if (t.active[t.prob[b]]) {
+    const double* v = V + (long long)i * ldv;
+    for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) d += v[e] * w[e];
+  }
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  __shared__ double red[kSegThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int q = 0; q < kSegThreads / 32; ++q) s += red[q];
+    partial[(long long)i * t.nchunks + b] = s;
+  }
+}
+
+__global__ void seg_reduce_kernel(SegTable t, const double* __restrict__ partial, double* __restrict__ h) {
+  const int p = blockIdx.x, i = blockIdx.y;
+  double s = 0.0;
+  for (int b = t.pchunk[p] + threadIdx.x; b < t.pchunk[p + 1]; b += blockDim.x) s += partial[(long long)i * t.nchunks + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += red[q];
+    h[(long long)i * t.K + p] = r;
+  }
+}
+
+__global__ void seg_update_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
+                                  const double* __restrict__ coef, double sign, double* __restrict__ w) {
+  const int b = blockIdx.x;
+  const int p = t.prob[b];
+  if (!t.active[p]) return;
+  __shared__ double c[512];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) c[i] = sign * coef[(long long)i * t.K + p];
+  __syncthreads();
+  // four elements per thread with independent accumulators keep several basis loads in flight
+  const long long lo = t.start[b], hi = t.end[b];
+  const int step = blockDim.x;
+  for (long long e0 = lo + threadIdx.x; e0 < hi; e0 += 4LL * step) {
+    const long long e1 = e0 + step, e2 = e0 + 2LL * step, e3 = e0 + 3LL * step;
+    const bool v1 = e1 < hi, v2 = e2 < hi, v3 = e3 < hi;
+    double a0 = w[e0], a1 = v1 ? w[e1] : 0.0, a2 = v2 ? w[e2] : 0.0, a3 = v3 ? w[e3] : 0.0;
+#pragma unroll 4
+    for (int i = 0; i < nvec; ++i) {
+      const double* vi = V + (long long)i * ldv;
+      const double ci = c[i];
+      a0 += ci * vi[e0];
+      if (v1) a1 += ci * vi[e1];
+      if (v2) a2 += ci * vi[e2];
+      if (v3) a3 += ci * vi[e3];
+    }
+    w[e0] = a0;
+    if (v1) w[e1] = a1;
+    if (v2) w[e2] = a2;
+    if (v3) w[e3] = a3;
+  }
+}
+
+__global__ void seg_scale_kernel(SegTable t, const double* __restrict__ s, const double* __restrict__ in,
+                                 double* __restrict__ out) {
+  const int b = blockIdx.x;
+  const int p = t.prob[b];
+  if (!t.active[p]) return;
+  const double f = s[p];
+  for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) out[e] = f * in[e];
+}
+
+__global__ void axpy64_kernel(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] += a * x[e];
 }
 
 // ------------------------------------------------------------------ forces / torques
@@ -786,9 +976,11 @@ template <typename T>
 void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu, T* out, double visc,
                   cudaStream_t st) {
   if (tg.n_tiles == 0) return;
-  PairArgs<T> A = make_args<T>(tg, src, lam_hat, mu, out, visc);
+  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  PairArgs<T> A = make_args<T>(tg, src, lam_hat, mu, out, visc, nt);
   ++t_launches;
-  pairs_kernel<T><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+  if (nt == 4) pairs_kernel<T, 4><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+  else pairs_kernel<T, 1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A);
 }
 template void launch_pairs<float>(const TargetSet&, const SourceSet&, const float*, const float*, float*, double, cudaStream_t);
 template void launch_pairs<double>(const TargetSet&, const SourceSet&, const double*, const double*, double*, double, cudaStream_t);
@@ -796,9 +988,55 @@ template void launch_pairs<double>(const TargetSet&, const SourceSet&, const dou
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu, double* out,
                      double visc, cudaStream_t st) {
   if (tg.n_tiles == 0) return;
-  PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc);
+  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
   ++t_launches;
-  pairs_dw_kernel<<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+  if (nt == 4) pairs_dw_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+  else pairs_dw_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A);
+}
+
+size_t pair_args64_bytes() { return sizeof(PairArgs<double>); }
+
+void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src, const double* lam_hat,
+                      const double* mu, double* out, double visc, int nodes_per_thread) {
+  PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nodes_per_thread);
+  std::memcpy(host_dst, &A, sizeof(A));
+}
+
+void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
+                          int nodes_per_thread, const double* lam, const double* mu, double* out,
+                          const long long* d_uoff, const long long* d_voff, cudaStream_t st) {
+  if (n_work == 0) return;
+  const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args);
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff};
+  ++t_launches;
+  if (double_float) {
+    if (nodes_per_thread == 4) pairs_dw_batch_kernel<4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
+    else pairs_dw_batch_kernel<1><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
+  } else {
+    if (nodes_per_thread == 4) pairs_batch_kernel<double, 4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
+    else pairs_batch_kernel<double, 1><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
+  }
+}
+
+void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
+                     double* h, cudaStream_t st) {
+  t_launches += 2;
+  seg_dots_kernel<<<dim3(t.nchunks, nvec), kSegThreads, 0, st>>>(t, V, ldv, w, partial);
+  seg_reduce_kernel<<<dim3(t.K, nvec), 128, 0, st>>>(t, partial, h);
+}
+void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
+                       double* w, cudaStream_t st) {
+  ++t_launches;
+  seg_update_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, nvec, V, ldv, coef, sign, w);
+}
+void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st) {
+  ++t_launches;
+  seg_scale_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, s, in, out);
+}
+void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st) {
+  ++t_launches;
+  axpy64_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, a, x, y);
 }
 
 template <typename T>
@@ -810,6 +1048,20 @@ void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st) {
   gemv_kernel<T><<<grid, kGemvThreads, 0, st>>>(b, x, y);
 }
 template void launch_gemv<float>(const GemvBatch<float>&, const float*, float*, cudaStream_t);
+
+void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, double* y64, cudaStream_t st) {
+  if (b.n_jobs == 0 || b.max_rows == 0) return;
+  const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
+  dim3 grid((b.max_rows + rows_per_cta - 1) / rows_per_cta, b.n_jobs);
+  ++t_launches;
+  if (y_dw) gemv_dw_kernel<false><<<grid, kGemvThreads, 0, st>>>(b, x, y_dw, nullptr);
+  else gemv_dw_kernel<true><<<grid, kGemvThreads, 0, st>>>(b, x, nullptr, y64);
+}
+
+void launch_split_dw(long long n, const double* in, float2* out, cudaStream_t st) {
+  ++t_launches;
+  split_dw_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, in, out);
+}
 template void launch_gemv<double>(const GemvBatch<double>&, const double*, double*, cudaStream_t);
 
 template <typename T>

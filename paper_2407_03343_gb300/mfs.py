@@ -53,7 +53,8 @@ class Sizes(C.Structure):
 
 class Timing(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("pair_launches", C.c_longlong), ("pair_ms", C.c_double),
-                ("pair_interactions", C.c_longlong), ("pair_kind", C.c_int), ("gemv_launches", C.c_longlong),
+                ("pair_interactions", C.c_longlong), ("pair_proxy", C.c_longlong),
+                ("pair_image_nodes", C.c_longlong), ("pair_kind", C.c_int), ("gemv_launches", C.c_longlong),
                 ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double)]
 
 
