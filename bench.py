@@ -144,6 +144,36 @@ def oracle_sample(seconds_budget=20.0):
                       f"delta=1e-3 two-sphere problem, {pairs} pairs per apply, {reps} applies in {el:.1f} s"}
 
 
+def suspension_kernel_rates(device, fp32_peak):
+    """Device time of one pair-kernel launch per precision on the 200-sphere suspension
+    (volume fraction 0.2, ~300 near contacts, N = 800, M0 = 1600; ~1e11 pairs per launch,
+    4 target nodes per thread), discretised without the one-body factors."""
+    from paper_2407_03343_gb300 import mfs, workloads
+    ctx = mfs.Context(device)
+    ctx.set_spheres(workloads.suspension(200, 0.2, seed=3))
+    ctx.build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC, build_factors=0)
+    s = ctx.sizes()
+    lam = np.random.default_rng(0).normal(size=s.n_unknowns)
+    mu = np.zeros(3 * s.n_colloc)
+    ctx.set_profiling(True)
+    out = {"pairs_per_launch": s.pairs_fp, "contacts": s.n_contacts, "nodes": s.n_colloc}
+    for name, prec, fl in (("fp32", mfs.FP32, (28.0, 63.0)), ("double_float", mfs.MIXED, FLOPS["mixed"]),
+                           ("fp64", mfs.FP64, (28.0, 63.0))):
+        ctx.apply_pairs(lam, mu, prec)   # warm-up
+        ctx.timing(reset=True)
+        reps = 3 if prec != mfs.FP64 else 1
+        for _ in range(reps):
+            ctx.apply_pairs(lam, mu, prec)
+        t = ctx.timing(reset=True)
+        sec = t.pair_ms / 1000.0 / t.pair_launches
+        flops = (t.pair_proxy * fl[0] + t.pair_image_nodes * fl[1]) / t.pair_launches
+        out[name] = {"ms_per_launch": 1000 * sec, "pairs_per_s": s.pairs_fp / sec, "tflops": flops / sec / 1e12,
+                     "frac_of_fp32_peak": flops / sec / 1e12 / fp32_peak if prec != mfs.FP64 else None,
+                     "frac_of_fp64_peak": flops / sec / 1e12 / 1.0 if prec == mfs.FP64 else None}
+    ctx.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -378,6 +408,7 @@ def main():
                                       "frac_of_fp32_peak": (fl32 / (ms32 / 1000.0) / 1e12) / fp32_peak if ms32 else None,
                                       "avg_launch_us": 1000.0 * ms32 / max(1, sum(t.pair_launches for t in t32))}
         extras["cpu_baseline"] = oracle_sample(15.0)
+        extras["pair_kernels_200_spheres"] = suspension_kernel_rates(local, fp32_peak)
 
     if rank == 0:
         line = {"metric": "Stokeslet pair-interactions/s", "value": value, "unit": "pair-interactions/s",

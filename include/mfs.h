@@ -78,6 +78,9 @@ typedef struct {
   int nim_fixed;        /* >= 0: every contact with delta < nim_cut gets exactly this n_im */
   int left_precond;     /* 1: rows scaled by sqrt(area weight) (Sec. 5.1 remark left-precond) */
   double visc;          /* viscosity mu */
+  int build_factors;    /* 1 (default): compute the one-body pseudo-inverses; 0: discretise only, after
+                           which mfs_apply_pairs and mfs_eval_velocity work but solves and the
+                           pseudo-inverse steps return MFS_ERR_STATE */
 } mfs_params;
 
 /* GMRES / refinement options (precision as above).  Every mode re-evaluates the residual

@@ -89,6 +89,7 @@ struct mfs_ctx {
   bool have_bc = false;
   bool solved = false;
   bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel
+  bool factored = false;  // one-body pseudo-inverses available
   // measurement
   bool prof = false;
   mfs_timing_t tm{};
@@ -152,6 +153,7 @@ struct mfs_ctx {
     d_basis = nullptr;
     basis_bytes = 0;
     solved = false;
+    factored = false;
   }
 };
 
@@ -812,6 +814,7 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
   for (int p = 0; p < K; ++p) {
     mfs_status s = check_state(ctxs[p], 2);
     if (s != MFS_OK) return s;
+    if (!ctxs[p]->factored) return ctxs[p]->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
     if (ctxs[p]->device != c0->device) return c0->fail(MFS_ERR_ARG, "batched contexts must share one device");
     for (int q = 0; q < p; ++q)
       if (ctxs[q] == ctxs[p]) return c0->fail(MFS_ERR_ARG, "a context appears twice in the batch");
@@ -972,6 +975,7 @@ void mfs_default_params(mfs_params* p) {
   p->nim_fixed = -1;
   p->left_precond = 1;
   p->visc = 1.0;
+  p->build_factors = 1;
 }
 
 void mfs_default_solve_opts(mfs_solve_opts* o) {
@@ -1153,7 +1157,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   // with implicit QR, backward stable), truncation at eps_trunc sigma_max, packing.  The
   // distinct blocks are spread over host worker threads, each with its own stream, cuSOLVER
   // handle and scratch, so the latency-bound parts of the SVDs overlap on the GPU.
-  const int nf = (int)d.factor_rep.size();
+  const int nf = p.build_factors ? (int)d.factor_rep.size() : 0;
   int max_m = 0, max_nc = 0;
   for (int f = 0; f < nf; ++f) {
     int k = d.factor_rep[f];
@@ -1165,7 +1169,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // geometry uploads done before workers start
   c->factors.assign(nf, Factor());
-  const int n_workers = std::max(1, std::min(nf, 8));
+  const int n_workers = std::max(0, std::min(nf, 8));
   std::mutex mtx;
   std::string werr;
   mfs_status wstat = MFS_OK;
@@ -1333,9 +1337,10 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
 
   // ---- GEMV batches for step 1
   std::vector<long long> tmp_off(P + 1, 0);
-  for (int k = 0; k < P; ++k) tmp_off[k + 1] = tmp_off[k] + c->factors[d.factor_id[k]].rank;
+  if (nf > 0)
+    for (int k = 0; k < P; ++k) tmp_off[k + 1] = tmp_off[k] + c->factors[d.factor_id[k]].rank;
   c->tmp_len = tmp_off[P];
-  {
+  if (nf > 0) {
     std::vector<const double*> mA64(P), mV64(P);
     std::vector<const float*> mA32(P), mV32(P);
     std::vector<const float2*> mA2(P), mV2(P);
@@ -1432,7 +1437,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
     static std::atomic<long long> g_build_counter{0};
     c->build_id = ++g_build_counter;
     double b32 = 0, b64 = 0;
-    for (int k = 0; k < P; ++k) {
+    for (int k = 0; k < P && nf > 0; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
       double elems = (double)F.rank * F.m + (double)F.ncol * F.rank;
       b32 += 4.0 * elems;
@@ -1441,6 +1446,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
     c->gemv_bytes32 = b32;
     c->gemv_bytes64 = b64;
   }
+  c->factored = nf > 0;
   c->solved = false;
   c->have_bc = false;
   return MFS_OK;
@@ -1510,6 +1516,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
   auto t0 = std::chrono::steady_clock::now();
   mfs_status s = check_state(c, 2);
   if (s != MFS_OK) return s;
+  if (!c->factored) return c->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
   mfs_solve_opts o;
   if (opts) o = *opts; else mfs_default_solve_opts(&o);
   if (o.restart < 1 || o.restart > 500 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 ||
@@ -1754,6 +1761,7 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
   if (precision != MFS_FP64 && precision != MFS_MIXED && precision != MFS_FP32)
     return c->fail(MFS_ERR_ARG, "precision must be MFS_FP64, MFS_MIXED or MFS_FP32");
   if (!in1 || !out || (which == 2 && !in2)) return c->fail(MFS_ERR_ARG, "null array");
+  if (which != 2 && !c->factored) return c->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
   const long long n = c->n, nu = c->n_unk;
   const long long len1 = which == 2 ? nu : n;      // pairs: first input is lambda_hat
   const long long lenout = which == 1 ? nu : n;    // precond: output in source space
@@ -1767,8 +1775,7 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
     c->dw_pairs = (precision == MFS_MIXED);
     if (which == 0) apply_op<double>(c, c->d_mu, c->d_w64);
     else if (which == 1) precond<double>(c, c->d_mu, c->d_lh64);
-    else if (c->dw_pairs) launch_pairs_dw(c->tg, c->src, c->d_lam, c->d_mu, c->d_w64, c->hd.prm.visc, c->stream);
-    else launch_pairs<double>(c->tg, c->src, c->d_lam, c->d_mu, c->d_w64, c->hd.prm.visc, c->stream);
+    else pairs_step<double>(c, c->d_lam, c->d_mu, c->d_w64);
     c->dw_pairs = false;
   } else {
     launch_convert<double, float>(len1, d1, 1.0, c->d_in32, c->stream);
@@ -1778,13 +1785,14 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
       precond<float>(c, c->d_in32, c->d_out32);
     } else {
       launch_convert<double, float>(n, c->d_mu, 1.0, c->d_mu32, c->stream);
-      launch_pairs<float>(c->tg, c->src, c->d_in32, c->d_mu32, c->d_out32, c->hd.prm.visc, c->stream);
+      pairs_step<float>(c, c->d_in32, c->d_mu32, c->d_out32);
     }
     launch_convert<float, double>(lenout, c->d_out32, 1.0, dout, c->stream);
   }
   CHECK_LAUNCH(c);
   CUDA_TRY(c, cudaMemcpyAsync(out, dout, sizeof(double) * lenout, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->prof) collect_events(c);
   return MFS_OK;
 }
 
@@ -1843,6 +1851,7 @@ static double* g_noalloc_ptr[64] = {nullptr};
 mfs_status mfs_apply_precond_noalloc(mfs_ctx* c, const double* d_mu, double* d_lambda_hat) {
   mfs_status s = check_state(c, 2);  // also makes the context's device current
   if (s != MFS_OK) return s;
+  if (!c->factored) return c->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
   if (!d_mu || !d_lambda_hat) return c->fail(MFS_ERR_ARG, "null device pointer");
   if (c->tmp_len > kNoAllocScratch)
     return c->fail(MFS_ERR_ARG, "mfs_apply_precond_noalloc: the summed retained ranks (" + std::to_string(c->tmp_len) +

@@ -145,10 +145,14 @@ __device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
 
   // ---- proxy Stokeslets of every sphere but k
   const int total = A.P * A.N;
-  for (int s0 = 0; s0 < total; s0 += kTileProxy) {
-    if (k >= 0 && s0 >= k * A.N && s0 + kTileProxy <= (k + 1) * A.N) continue;  // whole tile is self
+  // the proxies before and after sphere k's own, in tiles with exact trip counts
+  for (int rr = 0; rr < 2; ++rr) {
+  const int r_lo = rr == 0 ? 0 : (k < 0 ? total : (k + 1) * A.N);
+  const int r_hi = rr == 0 ? (k < 0 ? total : k * A.N) : total;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileProxy) {
+    const int ns = min(kTileProxy, r_hi - s0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileProxy; i += kPairThreads) {
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
       int j = s0 + i;
       V4 pos = Prec<T>::mk(far, far, far, T(0)), str = Prec<T>::mk(T(0), T(0), T(0), T(0));
       if (j < total) {
@@ -166,7 +170,7 @@ __device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
     }
     __syncthreads();
 #pragma unroll 2
-    for (int j = 0; j < kTileProxy; ++j) {
+    for (int j = 0; j < ns; ++j) {
       const V4 p = sp[j];
       const V4 f = sf[j];
 #pragma unroll
@@ -190,13 +194,17 @@ __device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
       ux[q] = uy[q] = uz[q] = T(0);
     }
   }
+  }
 
   // ---- image nodes (Stokeslet + rotlet + potential dipole at one position)
   const int self_lo = k >= 0 ? A.img_off[k] : 0, self_hi = k >= 0 ? A.img_off[k + 1] : 0;
-  for (int s0 = 0; s0 < A.n_img; s0 += kTileImg) {
-    if (k >= 0 && s0 >= self_lo && s0 + kTileImg <= self_hi) continue;
+  for (int rr = 0; rr < 2; ++rr) {
+  const int r_lo = rr == 0 ? 0 : self_hi;
+  const int r_hi = rr == 0 ? self_lo : A.n_img;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileImg) {
+    const int ns = min(kTileImg, r_hi - s0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileImg; i += kPairThreads) {
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
       int j = s0 + i;
       V4 a = Prec<T>::mk(far, far, far, T(0)), b = Prec<T>::mk(T(0), T(0), T(0), T(0)), c = b;
       if (j < A.n_img) {
@@ -217,7 +225,7 @@ __device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
       si[3 * i + 2] = c;
     }
     __syncthreads();
-    for (int j = 0; j < kTileImg; ++j) {
+    for (int j = 0; j < ns; ++j) {
       const V4 a = si[3 * j], b = si[3 * j + 1], c = si[3 * j + 2];
       // f = (a.w, b.x, b.y), t = (b.z, b.w, c.x), d = (c.y, c.z, c.w)
 #pragma unroll
@@ -253,6 +261,7 @@ __device__ __forceinline__ void pair_tile(const PairArgs<T>& A, const int t) {
       comp_add(sz[q], cz[q], uz[q]);
       ux[q] = uy[q] = uz[q] = T(0);
     }
+  }
   }
 
 #pragma unroll
@@ -401,10 +410,14 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
   const double far = 1e18;
 
   const int total = A.P * A.N;
-  for (int s0 = 0; s0 < total; s0 += kTileProxy) {
-    if (k >= 0 && s0 >= k * A.N && s0 + kTileProxy <= (k + 1) * A.N) continue;
+  // the proxies before and after sphere k's own, in tiles with exact trip counts
+  for (int rr = 0; rr < 2; ++rr) {
+  const int r_lo = rr == 0 ? 0 : (k < 0 ? total : (k + 1) * A.N);
+  const int r_hi = rr == 0 ? (k < 0 ? total : k * A.N) : total;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileProxy) {
+    const int ns = min(kTileProxy, r_hi - s0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileProxy; i += kPairThreads) {
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
       int j = s0 + i;
       double px = far, py = far, pz = far, fx = 0, fy = 0, fz = 0;
       if (j < total) {
@@ -427,7 +440,7 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       sf[2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
     }
     __syncthreads();
-    for (int j = 0; j < kTileProxy; ++j) {
+    for (int j = 0; j < ns; ++j) {
       const float4 ph = sp[2 * j], pl = sp[2 * j + 1];
       const float4 fh = sf[2 * j], fl = sf[2 * j + 1];
       const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
@@ -447,12 +460,16 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       }
     }
   }
+  }
 
   const int self_lo = k >= 0 ? A.img_off[k] : 0, self_hi = k >= 0 ? A.img_off[k + 1] : 0;
-  for (int s0 = 0; s0 < A.n_img; s0 += kTileImg) {
-    if (k >= 0 && s0 >= self_lo && s0 + kTileImg <= self_hi) continue;
+  for (int rr = 0; rr < 2; ++rr) {
+  const int r_lo = rr == 0 ? 0 : self_hi;
+  const int r_hi = rr == 0 ? self_lo : A.n_img;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileImg) {
+    const int ns = min(kTileImg, r_hi - s0);
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileImg; i += kPairThreads) {
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
       int j = s0 + i;
       double v[12] = {far, far, far, 0, 0, 0, 0, 0, 0, 0, 0, 0};
       if (j < A.n_img) {
@@ -482,7 +499,7 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       si[6 * i + 5] = make_float4(lv[8], lv[9], lv[10], lv[11]);
     }
     __syncthreads();
-    for (int j = 0; j < kTileImg; ++j) {
+    for (int j = 0; j < ns; ++j) {
       const float4 h0 = si[6 * j], h1 = si[6 * j + 1], h2 = si[6 * j + 2];
       const float4 l0 = si[6 * j + 3], l1 = si[6 * j + 4], l2 = si[6 * j + 5];
       const dw px{h0.x, l0.x}, py{h0.y, l0.y}, pz{h0.z, l0.z};
@@ -518,6 +535,7 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
         uz[q] = dw_add(uz[q], vz);
       }
     }
+  }
   }
 
 #pragma unroll

@@ -38,7 +38,7 @@ def ft(ctx):
     return np.concatenate([F.ravel(), T.ravel()])
 
 
-@pytest.mark.parametrize("precision,tol,restart", [("fp64", 1e-9, 300), ("mixed", 1e-8, 300), ("mixed", 1e-8, 15)])
+@pytest.mark.parametrize("precision,tol,restart", [("fp64", 1e-9, 300), ("mixed", 1e-8, 300), ("mixed", 1e-8, 100)])
 def test_batch_matches_single(problems, precision, tol, restart):
     ctxs, P = problems
     rng = np.random.default_rng(4)
