@@ -52,9 +52,11 @@ typedef enum {
 
 /* Precision of the solve and of the single-step entry points:
  *  MFS_FP64   native FP64 everywhere.
- *  MFS_MIXED  FP64 GMRES, FP64 pseudo-inverse factors; the pair sums of steps 2+3 run in
- *             double-float arithmetic (pairs of FP32 values, ~2^-46 relative) on the FP32
- *             pipes, which this GPU executes 74x faster than FP64.
+ *  MFS_MIXED  GMRES passes with the operator evaluated in double-float arithmetic (pairs of
+ *             FP32 values, ~2^-46 relative) on the FP32 pipes, which this GPU executes 74x
+ *             faster than FP64: pair sums of steps 2+3 and the pseudo-inverse GEMVs of step 1;
+ *             after each pass the residual is re-evaluated with the native FP64 operator and
+ *             the correction equation solved again (iterative refinement).
  *  MFS_FP32   FP32 inner GMRES on an all-FP32 operator with FP64 iterative refinement;
  *             converges only when B_k^+ amplifies by well under 1/eps_FP32, i.e. not with
  *             images and the paper's truncation 5e-12 (returns MFS_ERR_NOT_CONVERGED). */
@@ -231,6 +233,11 @@ typedef struct {
   long long gemv_launches;
   double gemv_ms;
   double gemv_bytes;             /* factor bytes read by those launches */
+  /* the pair statistics split by precision (index MFS_FP64, MFS_MIXED, MFS_FP32) */
+  long long by_kind_launches[3];
+  double by_kind_ms[3];
+  long long by_kind_proxy[3];
+  long long by_kind_image_nodes[3];
 } mfs_timing_t;
 mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
 /* Copies the counters; reset != 0 zeroes them afterwards. */

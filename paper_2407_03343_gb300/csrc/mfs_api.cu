@@ -94,6 +94,7 @@ struct mfs_ctx {
   bool prof = false;
   mfs_timing_t tm{};
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_pool;
+  std::vector<int> ev_pair_kind;  // precision of each pair launch in ev_pair
   long long pairs_per_apply = 0, proxy_per_apply = 0, image_per_apply = 0;
   long long build_id = 0;
   struct BatchPlan* batch = nullptr;  // cached lockstep-batch workspace (owned when this is the first context)
@@ -225,12 +226,18 @@ void timed(mfs_ctx* c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& list, F
 }
 // folds finished event pairs into the counters (call after a stream synchronisation)
 void collect_events(mfs_ctx* c) {
-  for (auto& e : c->ev_pair) {
+  for (size_t i = 0; i < c->ev_pair.size(); ++i) {
+    auto& e = c->ev_pair[i];
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.pair_ms += ms;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+      c->tm.pair_ms += ms;
+      int kind = i < c->ev_pair_kind.size() ? c->ev_pair_kind[i] : 0;
+      if (kind >= 0 && kind < 3) c->tm.by_kind_ms[kind] += ms;
+    }
     c->ev_pool.push_back(e);
   }
   c->ev_pair.clear();
+  c->ev_pair_kind.clear();
   for (auto& e : c->ev_gemv) {
     float ms = 0;
     if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.gemv_ms += ms;
@@ -277,6 +284,11 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
   c->tm.pair_proxy += c->proxy_per_apply;
   c->tm.pair_image_nodes += c->image_per_apply;
   c->tm.pair_kind = sizeof(T) == 4 ? MFS_FP32 : (c->dw_pairs ? MFS_MIXED : MFS_FP64);
+  const int kind = c->tm.pair_kind;
+  c->tm.by_kind_launches[kind] += 1;
+  c->tm.by_kind_proxy[kind] += c->proxy_per_apply;
+  c->tm.by_kind_image_nodes[kind] += c->image_per_apply;
+  if (c->prof) c->ev_pair_kind.push_back(kind);
 }
 
 // out = G_hat mu
@@ -582,7 +594,7 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
     B->gV.n_jobs = (int)mV.size(); B->gV.max_rows = maxV; B->gV.job_prob = djp; B->gV.active = B->d_active;
   }
   // vector chunks, each inside one problem
-  const long long chunk = 4096;
+  const long long chunk = 1024;  // enough chunks to fill the GPU for batches of small problems
   std::vector<int> cprob, pchunk(1, 0);
   std::vector<long long> cs, ce;
   for (int p = 0; p < K; ++p) {
@@ -662,11 +674,16 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
   c->tm.gemv_launches += 2;
   c->tm.pair_launches += 1;
   c->tm.pair_kind = R.dw ? MFS_MIXED : MFS_FP64;
+  const int kind = c->tm.pair_kind;
+  c->tm.by_kind_launches[kind] += 1;
+  if (c->prof) c->ev_pair_kind.push_back(kind);
   for (int p = 0; p < B->K; ++p)
     if (R.act[p]) {
       c->tm.pair_interactions += B->pairs_p[p];
       c->tm.pair_proxy += B->proxy_p[p];
       c->tm.pair_image_nodes += B->image_p[p];
+      c->tm.by_kind_proxy[kind] += B->proxy_p[p];
+      c->tm.by_kind_image_nodes[kind] += B->image_p[p];
       c->tm.gemv_bytes += B->key[p]->gemv_bytes64;
     }
 }
@@ -883,7 +900,13 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     std::vector<int> live(K);
     for (int p = 0; p < K; ++p) live[p] = bnorm[p] > 0;
     if ((s = set_active(R, live)) != MFS_OK) return s;
-    batch_apply(R, B->x, B->w);
+    {
+      // refinement residual with the native FP64 operator (see mfs_solve)
+      const bool dw = R.dw;
+      R.dw = false;
+      batch_apply(R, B->x, B->w);
+      R.dw = dw;
+    }
     launch_sub((int)n, B->wb, B->w, B->r, R.st);
     CHECK_LAUNCH(c0);
     if ((s = batch_norms(R, B->r, rn)) != MFS_OK) return s;
@@ -1560,7 +1583,11 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
         CUDA_TRY(c, cudaMemcpyAsync(c->d_h + 4 * 512 + 8, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
         launch_update<double>(n, 1, c->d_w64, n, c->d_h + 4 * 512 + 8, 1.0, c->d_mu, c->stream);
       }
+      // refinement residual with the native FP64 operator: the double-float passes then only
+      // have to contract the error, and the final accuracy is that of FP64
+      c->dw_pairs = false;
       apply_op<double>(c, c->d_mu, c->d_w64);
+      c->dw_pairs = (o.precision == MFS_MIXED);
       launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
       CHECK_LAUNCH(c);
       double rprev = rn;

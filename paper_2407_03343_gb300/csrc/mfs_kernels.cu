@@ -378,6 +378,64 @@ __device__ __forceinline__ dw dw_rsqrt(dw x) {
   return fast_two_sum(s, __fmul_rn(__fmul_rn(0.5f, s), h));
 }
 
+// Compensated evaluation for the pair kernel (in the style of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005): a product keeps its exact
+// rounding error plus the first-order cross terms, a sum keeps the TwoSum error plus the low
+// parts, and neither renormalises; the low part then stays within a few ulps of the high part
+// scaled by the operands' magnitude, which bounds every absolute error by ~2^-46 of the
+// operands.  Renormalisation is kept where cancellation could let the low part outgrow the
+// high part (differences of positions and dot products) and at every accumulation.
+__device__ __forceinline__ dw mul_u(dw x, dw y) {
+  float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, e);
+  e = __fmaf_rn(x.l, y.h, e);
+  return {p, e};
+}
+__device__ __forceinline__ dw add_u(dw x, dw y) {
+  dw s = two_sum(x.h, y.h);
+  return {s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l))};
+}
+__device__ __forceinline__ dw neg(dw x) { return {-x.h, -x.l}; }
+// u += t with the running sum renormalised every time: its partial sums can exceed the final
+// value by ~1e9 under cancellation, so its low word must stay within an ulp of the high word
+__device__ __forceinline__ void acc_u(dw& u, dw t) { u = dw_add(u, t); }
+// x - y for positions: the difference is never below ~1e-3 of the radius, far above the low parts
+__device__ __forceinline__ dw sub_pos(dw x, dw y) {
+  dw s = two_sum(x.h, -y.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(x.l, y.l)));
+}
+// a.b for three double-word pairs, renormalised (the sum may cancel)
+__device__ __forceinline__ dw dot3_u(dw a0, dw a1, dw a2, dw b0, dw b1, dw b2) {
+  dw p0 = mul_u(a0, b0), p1 = mul_u(a1, b1), p2 = mul_u(a2, b2);
+  dw s1 = two_sum(p0.h, p1.h);
+  dw s2 = two_sum(s1.h, p2.h);
+  float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(p2.l, s1.l)), s2.l);
+  return two_sum(s2.h, lo);
+}
+// |d|^2 (all terms positive, no cancellation)
+__device__ __forceinline__ dw norm2_u(dw d0, dw d1, dw d2) {
+  dw p0 = two_prod(d0.h, d0.h), p1 = two_prod(d1.h, d1.h), p2 = two_prod(d2.h, d2.h);
+  p0.l = __fmaf_rn(__fadd_rn(d0.h, d0.h), d0.l, p0.l);
+  p1.l = __fmaf_rn(__fadd_rn(d1.h, d1.h), d1.l, p1.l);
+  p2.l = __fmaf_rn(__fadd_rn(d2.h, d2.h), d2.l, p2.l);
+  dw s1 = two_sum(p0.h, p1.h);
+  dw s2 = two_sum(s1.h, p2.h);
+  float lo = __fadd_rn(__fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(p2.l, s1.l)), s2.l);
+  return fast_two_sum(s2.h, lo);
+}
+__device__ __forceinline__ dw rsqrt_u(dw x) {
+  float s = rsqrtf(x.h);
+  s = __fmul_rn(s, __fmaf_rn(__fmul_rn(-0.5f, x.h), __fmul_rn(s, s), 1.5f));
+  dw e = mul_u(x, two_prod(s, s));
+  float h = __fsub_rn(__fsub_rn(1.0f, e.h), e.l);
+  return fast_two_sum(s, __fmul_rn(__fmul_rn(0.5f, s), h));
+}
+__device__ __forceinline__ dw times3_u(dw x) {
+  dw c = two_prod(x.h, 3.0f);
+  return {c.h, __fmaf_rn(x.l, 3.0f, c.l)};
+}
+
 struct __align__(16) DWPos {
   float xh, yh, zh, pad0;
   float xl, yl, zl, pad1;
@@ -446,18 +504,22 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
 #pragma unroll
       for (int q = 0; q < NT; ++q) {
-        dw dx = dw_sub(x[q], dw{ph.x, pl.x});
-        dw dy = dw_sub(y[q], dw{ph.y, pl.y});
-        dw dz = dw_sub(z[q], dw{ph.z, pl.z});
-        dw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
-        dw ir = dw_rsqrt(r2);
-        dw ir2 = dw_mul(ir, ir);
-        dw rf = dw_add(dw_add(dw_mul(dx, fx), dw_mul(dy, fy)), dw_mul(dz, fz));
-        dw c = dw_mul(rf, ir2);
-        ux[q] = dw_add(ux[q], dw_mul(ir, dw_add(fx, dw_mul(c, dx))));
-        uy[q] = dw_add(uy[q], dw_mul(ir, dw_add(fy, dw_mul(c, dy))));
-        uz[q] = dw_add(uz[q], dw_mul(ir, dw_add(fz, dw_mul(c, dz))));
+        dw dx = sub_pos(x[q], dw{ph.x, pl.x});
+        dw dy = sub_pos(y[q], dw{ph.y, pl.y});
+        dw dz = sub_pos(z[q], dw{ph.z, pl.z});
+        dw ir = rsqrt_u(norm2_u(dx, dy, dz));
+        dw ir2 = mul_u(ir, ir);
+        dw c = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
+        acc_u(ux[q], mul_u(ir, add_u(fx, mul_u(c, dx))));
+        acc_u(uy[q], mul_u(ir, add_u(fy, mul_u(c, dy))));
+        acc_u(uz[q], mul_u(ir, add_u(fz, mul_u(c, dz))));
       }
+    }
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      ux[q] = two_sum(ux[q].h, ux[q].l);
+      uy[q] = two_sum(uy[q].h, uy[q].l);
+      uz[q] = two_sum(uz[q].h, uz[q].l);
     }
   }
   }
@@ -508,32 +570,34 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       const dw qx{h2.y, l2.y}, qy{h2.z, l2.z}, qz{h2.w, l2.w};
 #pragma unroll
       for (int q = 0; q < NT; ++q) {
-        dw dx = dw_sub(x[q], px), dy = dw_sub(y[q], py), dz = dw_sub(z[q], pz);
-        dw r2 = dw_add(dw_add(dw_mul(dx, dx), dw_mul(dy, dy)), dw_mul(dz, dz));
-        dw ir = dw_rsqrt(r2);
-        dw ir2 = dw_mul(ir, ir);
-        dw ir3 = dw_mul(ir, ir2);
+        dw dx = sub_pos(x[q], px), dy = sub_pos(y[q], py), dz = sub_pos(z[q], pz);
+        dw ir = rsqrt_u(norm2_u(dx, dy, dz));
+        dw ir2 = mul_u(ir, ir);
+        dw ir3 = mul_u(ir, ir2);
         // Stokeslet
-        dw rf = dw_add(dw_add(dw_mul(dx, fx), dw_mul(dy, fy)), dw_mul(dz, fz));
-        dw cs = dw_mul(rf, ir2);
-        dw vx = dw_mul(ir, dw_add(fx, dw_mul(cs, dx)));
-        dw vy = dw_mul(ir, dw_add(fy, dw_mul(cs, dy)));
-        dw vz = dw_mul(ir, dw_add(fz, dw_mul(cs, dz)));
+        dw cs = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
+        acc_u(ux[q], mul_u(ir, add_u(fx, mul_u(cs, dx))));
+        acc_u(uy[q], mul_u(ir, add_u(fy, mul_u(cs, dy))));
+        acc_u(uz[q], mul_u(ir, add_u(fz, mul_u(cs, dz))));
         // rotlet (t x r) / r^3
-        vx = dw_add(vx, dw_mul(ir3, dw_sub(dw_mul(ty, dz), dw_mul(tz, dy))));
-        vy = dw_add(vy, dw_mul(ir3, dw_sub(dw_mul(tz, dx), dw_mul(tx, dz))));
-        vz = dw_add(vz, dw_mul(ir3, dw_sub(dw_mul(tx, dy), dw_mul(ty, dx))));
+        acc_u(ux[q], mul_u(ir3, add_u(mul_u(ty, dz), neg(mul_u(tz, dy)))));
+        acc_u(uy[q], mul_u(ir3, add_u(mul_u(tz, dx), neg(mul_u(tx, dz)))));
+        acc_u(uz[q], mul_u(ir3, add_u(mul_u(tx, dy), neg(mul_u(ty, dx)))));
         // potential dipole -d / r^3 + 3 (d.r) r / r^5
-        dw rd = dw_add(dw_add(dw_mul(dx, qx), dw_mul(dy, qy)), dw_mul(dz, qz));
-        dw c3 = dw_mul(dw_mul(rd, ir3), ir2);
-        c3 = dw_mul_f(c3, 3.0f);
-        vx = dw_add(vx, dw_sub(dw_mul(c3, dx), dw_mul(ir3, qx)));
-        vy = dw_add(vy, dw_sub(dw_mul(c3, dy), dw_mul(ir3, qy)));
-        vz = dw_add(vz, dw_sub(dw_mul(c3, dz), dw_mul(ir3, qz)));
-        ux[q] = dw_add(ux[q], vx);
-        uy[q] = dw_add(uy[q], vy);
-        uz[q] = dw_add(uz[q], vz);
+        dw c3 = times3_u(mul_u(mul_u(dot3_u(dx, dy, dz, qx, qy, qz), ir3), ir2));
+        acc_u(ux[q], mul_u(c3, dx));
+        acc_u(uy[q], mul_u(c3, dy));
+        acc_u(uz[q], mul_u(c3, dz));
+        acc_u(ux[q], neg(mul_u(ir3, qx)));
+        acc_u(uy[q], neg(mul_u(ir3, qy)));
+        acc_u(uz[q], neg(mul_u(ir3, qz)));
       }
+    }
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      ux[q] = two_sum(ux[q].h, ux[q].l);
+      uy[q] = two_sum(uy[q].h, uy[q].l);
+      uz[q] = two_sum(uz[q].h, uz[q].l);
     }
   }
   }

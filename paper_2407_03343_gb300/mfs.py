@@ -55,7 +55,9 @@ class Timing(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("pair_launches", C.c_longlong), ("pair_ms", C.c_double),
                 ("pair_interactions", C.c_longlong), ("pair_proxy", C.c_longlong),
                 ("pair_image_nodes", C.c_longlong), ("pair_kind", C.c_int), ("gemv_launches", C.c_longlong),
-                ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double)]
+                ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double),
+                ("by_kind_launches", C.c_longlong * 3), ("by_kind_ms", C.c_double * 3),
+                ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3)]
 
 
 class MfsError(RuntimeError):
