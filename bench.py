@@ -145,6 +145,20 @@ def oracle_sample(seconds_budget=20.0):
                       f"delta=1e-3 two-sphere problem, {pairs} pairs per apply, {reps} applies in {el:.1f} s"}
 
 
+def reduce_over_ranks(total_ms, pairs, device):
+    """(max over ranks of the timed milliseconds, sum over ranks of the pairs); identity on one
+    rank.  device: the tensor device of the process group's backend (CUDA for NCCL, None = CPU)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(pairs)
+    import torch
+    tt = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(pt)
+    return float(tt.item()), float(pt.item())
+
+
 def suspension_kernel_rates(device, fp32_peak):
     """Device time of one pair-kernel launch per precision on the 200-sphere suspension
     (volume fraction 0.2, ~300 near contacts, N = 800, M0 = 1600; ~1e11 pairs per launch,
@@ -315,15 +329,9 @@ def main():
     gemv_bytes = sum(t.gemv_bytes for t in tms)
     gemv_launches = sum(t.gemv_launches for t in tms)
 
-    # max over ranks of the timed region
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        pt = torch.tensor([float(pairs)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(pt)
-        total_ms_max, pairs_all = float(tt.item()), float(pt.item())
-    else:
-        total_ms_max, pairs_all = total_ms, float(pairs)
+    # max over ranks of the timed region, pairs summed over ranks (weak scaling: every rank
+    # solves its own sweep, no data-path collective)
+    total_ms_max, pairs_all = reduce_over_ranks(total_ms, pairs, dev if world > 1 else None)
     value = pairs_all / (total_ms_max / 1000.0)
 
     # ---- roofline of the dominant kernel (pair kernel), from its own launch events:
