@@ -6,7 +6,8 @@ log-spaced in [1e-3, 1], three relative motions each (squeezing, shearing, count
 N = 800 proxy Stokeslets on R_p = 0.63, M0 = 1600 basic collocation nodes, images and caps by
 the n_im rule (<= 20 per contact, <= 60 image sources), one-body truncation 5e-12, GMRES
 tolerance 1e-6.  One step = the 54 resistance solves (steps 1-3 of the preconditioned apply
-inside GMRES, FP64 residual, lambda = B^+ mu, forces and torques); the 18 discretisations and
+inside GMRES, FP64 residual, lambda = B^+ mu, forces and torques), all 54 in one lockstep batch
+in which the three motions of a geometry share its factor reads; the 18 discretisations and
 their one-body SVDs are built once before timing (reported as setup_s).
 
 metric   Stokeslet pair-interactions/s: (target node, vector source) pairs evaluated by the
@@ -263,20 +264,21 @@ def main():
     dev = torch.device("cuda", local)
     d_vel = {m: (torch.tensor(v, dtype=torch.float64, device=dev), torch.tensor(w, dtype=torch.float64, device=dev))
              for m, (v, w) in vel.items()}
-    d_ft = [(torch.zeros((2, 3), dtype=torch.float64, device=dev), torch.zeros((2, 3), dtype=torch.float64, device=dev))
-            for _ in gaps]
+    # the 54 problems: every geometry with each of the three motions, one lockstep batch in which
+    # the three right-hand sides of a geometry share its factor reads
+    probs = [c for _ in MOTIONS for c in ctxs]
+    vel_host = [vel[m] for m in MOTIONS for _ in ctxs]
+    d_F = [torch.zeros((2, 3), dtype=torch.float64, device=dev) for _ in probs]
+    d_T = [torch.zeros((2, 3), dtype=torch.float64, device=dev) for _ in probs]
+    v_ptrs = [d_vel[m][0].data_ptr() for m in MOTIONS for _ in ctxs]
+    w_ptrs = [d_vel[m][1].data_ptr() for m in MOTIONS for _ in ctxs]
+    F_ptrs = [t.data_ptr() for t in d_F]
+    T_ptrs = [t.data_ptr() for t in d_T]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     main_stream = torch.cuda.current_stream()
 
     def device_step():
-        for m in MOTIONS:
-            v, w = d_vel[m]
-            for c in ctxs:
-                c.set_rigid_velocities_device(v.data_ptr(), w.data_ptr())
-            infos = mfs.batch_solve(ctxs, opts)
-            for c, (F, T) in zip(ctxs, d_ft):
-                c.forces_torques_device(F.data_ptr(), T.data_ptr())
-        return infos
+        return mfs.batch_solve_rhs_device(probs, v_ptrs, w_ptrs, F_ptrs, T_ptrs, opts)
 
     def timed_step(fn):
         start = torch.cuda.Event(enable_timing=True)
@@ -371,14 +373,7 @@ def main():
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for m in MOTIONS:
-            v, w = vel[m]
-            vh, wh = np.ascontiguousarray(v), np.ascontiguousarray(w)
-            for c in ctxs:
-                c.set_rigid_velocities(vh, wh)
-            mfs.batch_solve(ctxs, opts)
-            for c in ctxs:
-                c.forces_torques()
+        mfs.batch_solve_rhs(probs, vel_host, opts)   # host velocities in, host forces/torques out
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     h2d = len(MOTIONS) * len(ctxs) * 2 * 6 * 8
     d2h = len(MOTIONS) * len(ctxs) * 2 * 6 * 8
@@ -391,18 +386,10 @@ def main():
         o64 = mfs.default_solve_opts(precision="fp64", tol=1e-6)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for m in MOTIONS:
-            v, w = vel[m]
-            for c in ctxs:
-                c.set_rigid_velocities(v, w)
-            mfs.batch_solve(ctxs, o64)
+        mfs.batch_solve_rhs(probs, vel_host, o64)
         t64 = time.perf_counter() - t0
         t0 = time.perf_counter()
-        for m in MOTIONS:
-            v, w = vel[m]
-            for c in ctxs:
-                c.set_rigid_velocities(v, w)
-            mfs.batch_solve(ctxs, opts)
+        mfs.batch_solve_rhs(probs, vel_host, opts)
         tmix = time.perf_counter() - t0
         for c in ctxs:
             c.timing(reset=True)

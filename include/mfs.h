@@ -218,6 +218,21 @@ mfs_status mfs_apply_precond_noalloc(mfs_ctx* ctx, const double* d_mu, double* d
 mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve_opts* opts,
                            mfs_solve_info* infos);
 
+/* Several right-hand sides per geometry (a resistance matrix needs 6P of them, a sweep of
+ * motions several): problem i is (ctxs[i], v[i], omega[i]) with v[i], omega[i] of P_i*3 values;
+ * contexts MAY repeat.  All problems run in one lockstep batch as in mfs_batch_solve, and the
+ * pseudo-inverse factors of a repeated context are read once per apply for all its right-hand
+ * sides.  Forces and torques of problem i go to F[i], T[i] (P_i*3 each, entries may be NULL);
+ * each context afterwards holds the solution of its last problem in the list (for
+ * mfs_eval_velocity / mfs_get_strengths).  Background flows are the contexts' own.
+ * MFS_FP64 and MFS_MIXED only.  The _device variant takes device pointers for v, omega, F, T. */
+mfs_status mfs_batch_solve_rhs(int n_problems, mfs_ctx* const* ctxs, const double* const* v,
+                               const double* const* omega, const mfs_solve_opts* opts,
+                               mfs_solve_info* infos, double* const* F, double* const* T);
+mfs_status mfs_batch_solve_rhs_device(int n_problems, mfs_ctx* const* ctxs, const double* const* d_v,
+                                      const double* const* d_omega, const mfs_solve_opts* opts,
+                                      mfs_solve_info* infos, double* const* d_F, double* const* d_T);
+
 /* ---- measurement ----
  * With profiling on, the context brackets each launch of the pair kernel (steps 2+3) and of the
  * pseudo-inverse GEMVs (step 1) with CUDA events on its stream and accumulates their device

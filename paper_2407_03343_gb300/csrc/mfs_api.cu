@@ -463,9 +463,12 @@ struct BatchPlan {
   std::vector<long long> voff, uoff, toff;
   std::vector<long long> pairs_p, proxy_p, image_p;
   std::vector<void*> allocs;
-  void* d_args = nullptr;
-  int2* d_work = nullptr;
-  int n_work = 0;
+  void* d_args = nullptr;    // per-problem kernel arguments for 4 nodes per thread
+  void* d_args1 = nullptr;   // and for 1 node per thread
+  int2* d_work = nullptr;    // (problem, tile) lists for both tilings
+  int2* d_work1 = nullptr;
+  int n_work = 0, n_work1 = 0;
+  std::vector<int> tiles4;   // large tiles per problem, to pick the tiling of each launch
   int* d_active = nullptr;
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
@@ -473,6 +476,8 @@ struct BatchPlan {
   double *wb = nullptr, *x = nullptr, *r = nullptr, *e = nullptr, *w = nullptr, *lh = nullptr, *tmp = nullptr,
          *lam = nullptr, *partial = nullptr, *hbuf = nullptr, *coef = nullptr, *scl = nullptr;
   float2 *x2 = nullptr, *t2 = nullptr;
+  std::vector<long long> boff;           // per problem: offset of its 3 P values in bc / F / T
+  double *bc_v = nullptr, *bc_w = nullptr, *out_F = nullptr, *out_T = nullptr;
   double* basis = nullptr;
   size_t basis_cap = 0;
   double* hpin = nullptr;  // pinned host staging for the Arnoldi coefficients
@@ -531,49 +536,76 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   B->n_total = B->voff[K];
   B->u_total = B->uoff[K];
   B->t_total = B->toff[K];
-  B->nt = pair_nodes_per_thread((int)std::min<long long>(tiles_large, 1 << 30));
-  // pair kernel arguments and work list
+  (void)tiles_large;
+  // pair kernel arguments and work lists for both tilings; each launch picks the tiling from
+  // the tiles of the problems still active (the lockstep tail may hold a single problem)
   const size_t asz = pair_args64_bytes();
-  std::vector<char> args(asz * K);
-  std::vector<int2> work;
+  std::vector<char> args4(asz * K), args1(asz * K);
+  std::vector<int2> work4, work1;
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
-    fill_pair_args64(args.data() + asz * p, c->tg, c->src, nullptr, nullptr, nullptr, c->hd.prm.visc, B->nt);
-    int nt_tiles = B->nt == 4 ? c->tg.n_tiles : c->tg.n_tiles1;
-    for (int t = 0; t < nt_tiles; ++t) work.push_back(make_int2(p, t));
+    fill_pair_args64(args4.data() + asz * p, c->tg, c->src, nullptr, nullptr, nullptr, c->hd.prm.visc, 4);
+    fill_pair_args64(args1.data() + asz * p, c->tg, c->src, nullptr, nullptr, nullptr, c->hd.prm.visc, 1);
+    for (int t = 0; t < c->tg.n_tiles; ++t) work4.push_back(make_int2(p, t));
+    for (int t = 0; t < c->tg.n_tiles1; ++t) work1.push_back(make_int2(p, t));
+    B->tiles4.push_back(c->tg.n_tiles);
   }
-  B->n_work = (int)work.size();
-  B->d_args = B->alloc<char>(args.size());
-  bool ok = B->d_args && cudaMemcpy(B->d_args, args.data(), args.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && put(B, B->d_work, work) && put(B, B->d_uoff, B->uoff) && put(B, B->d_voff, B->voff);
+  B->n_work = (int)work4.size();
+  B->n_work1 = (int)work1.size();
+  B->d_args = B->alloc<char>(args4.size());
+  B->d_args1 = B->alloc<char>(args1.size());
+  bool ok = B->d_args && B->d_args1 &&
+            cudaMemcpy(B->d_args, args4.data(), args4.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(B->d_args1, args1.data(), args1.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && put(B, B->d_work, work4) && put(B, B->d_work1, work1) && put(B, B->d_uoff, B->uoff) &&
+       put(B, B->d_voff, B->voff);
   B->d_active = B->alloc<int>(K);
   ok = ok && B->d_active;
-  // GEMV jobs: every sphere of every problem
+  // GEMV jobs: every sphere of every problem, with the problems that share a context (several
+  // right-hand sides on one geometry) adjacent, so a factor matrix is read once for all of them
   std::vector<const double*> mA, mV;
   std::vector<const float2*> mA2, mV2;
   std::vector<int> rA, cA, lA, rV, cV, lV, jp;
   std::vector<long long> xA, yA, xV, yV;
   int maxA = 0, maxV = 0;
-  for (int p = 0; p < K && ok; ++p) {
+  std::vector<std::vector<long long>> ptoff(K);
+  for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
+    long long t = 0;
+    ptoff[p].push_back(0);
+    for (int kk = 0; kk < c->hd.P; ++kk) {
+      t += c->factors[c->hd.factor_id[kk]].rank;
+      ptoff[p].push_back(t);
+    }
+  }
+  std::vector<int> seen(K, 0);
+  for (int p0 = 0; p0 < K && ok; ++p0) {
+    if (seen[p0]) continue;
+    mfs_ctx* c = ctxs[p0];
     const HostDisc& d = c->hd;
-    long long toff = 0;
+    std::vector<int> group;
+    for (int p = p0; p < K; ++p)
+      if (ctxs[p] == c) {
+        group.push_back(p);
+        seen[p] = 1;
+      }
     for (int k = 0; k < d.P; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
-      mA.push_back(F.A64);
-      mV.push_back(F.V64);
-      mA2.push_back(F.A2);
-      mV2.push_back(F.V2);
-      rA.push_back(F.rank); cA.push_back(F.m); lA.push_back(F.ldA);
-      xA.push_back(B->voff[p] + 3LL * d.colloc_off[k]);
-      yA.push_back(B->toff[p] + toff);
-      rV.push_back(F.ncol); cV.push_back(F.rank); lV.push_back(F.ldV);
-      xV.push_back(B->toff[p] + toff);
-      yV.push_back(B->uoff[p] + d.unk_off[k]);
-      jp.push_back(p);
-      toff += F.rank;
-      maxA = std::max(maxA, F.rank);
-      maxV = std::max(maxV, F.ncol);
+      for (int p : group) {
+        mA.push_back(F.A64);
+        mV.push_back(F.V64);
+        mA2.push_back(F.A2);
+        mV2.push_back(F.V2);
+        rA.push_back(F.rank); cA.push_back(F.m); lA.push_back(F.ldA);
+        xA.push_back(B->voff[p] + 3LL * d.colloc_off[k]);
+        yA.push_back(B->toff[p] + ptoff[p][k]);
+        rV.push_back(F.ncol); cV.push_back(F.rank); lV.push_back(F.ldV);
+        xV.push_back(B->toff[p] + ptoff[p][k]);
+        yV.push_back(B->uoff[p] + d.unk_off[k]);
+        jp.push_back(p);
+        maxA = std::max(maxA, F.rank);
+        maxV = std::max(maxV, F.ncol);
+      }
     }
   }
   const double** dmA = nullptr;
@@ -625,6 +657,10 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
        (B->hbuf = B->alloc<double>((size_t)(2 * kMaxBatchVec + 1) * K)) &&
        (B->coef = B->alloc<double>((size_t)kMaxBatchVec * K)) && (B->scl = B->alloc<double>(K)) &&
        (B->x2 = B->alloc<float2>(n)) && (B->t2 = B->alloc<float2>(B->t_total));
+  B->boff.assign(K + 1, 0);
+  for (int p = 0; p < K; ++p) B->boff[p + 1] = B->boff[p] + 3LL * ctxs[p]->P;
+  ok = ok && (B->bc_v = B->alloc<double>(B->boff[K])) && (B->bc_w = B->alloc<double>(B->boff[K])) &&
+       (B->out_F = B->alloc<double>(B->boff[K])) && (B->out_T = B->alloc<double>(B->boff[K]));
   ok = ok && cudaMallocHost(&B->hpin, sizeof(double) * (2 * kMaxBatchVec + 1) * K) == cudaSuccess &&
        cudaMallocHost(&B->apin, sizeof(int) * K) == cudaSuccess && cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
@@ -667,9 +703,17 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
       launch_gemv<double>(B->gV, B->tmp, B->lh, R.st);
     }
   });
+  long long active_tiles = 0;
+  for (int p = 0; p < B->K; ++p)
+    if (R.act[p]) active_tiles += B->tiles4[p];
+  const int nt = pair_nodes_per_thread((int)std::min<long long>(active_tiles, 1 << 30));
   timed(c, c->ev_pair, [&] {
-    launch_pairs_batch64(R.dw, B->d_args, B->d_work, B->n_work, B->d_active, B->nt, B->lh, in, out, B->d_uoff,
-                         B->d_voff, R.st);
+    if (nt == 4)
+      launch_pairs_batch64(R.dw, B->d_args, B->d_work, B->n_work, B->d_active, 4, B->lh, in, out, B->d_uoff,
+                           B->d_voff, R.st);
+    else
+      launch_pairs_batch64(R.dw, B->d_args1, B->d_work1, B->n_work1, B->d_active, 1, B->lh, in, out, B->d_uoff,
+                           B->d_voff, R.st);
   });
   c->tm.gemv_launches += 2;
   c->tm.pair_launches += 1;
@@ -825,7 +869,20 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
   return MFS_OK;
 }
 
-mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos) {
+// Boundary data and outputs of a batch: from and to the contexts themselves (distinct contexts),
+// or per problem from caller arrays (contexts may repeat: several right-hand sides per geometry).
+struct BatchIO {
+  const double* const* v = nullptr;  // null: take each context's own boundary data
+  const double* const* w = nullptr;
+  bool in_device = false;
+  double* const* F = nullptr;        // null: forces/torques go to the contexts
+  double* const* T = nullptr;
+  bool out_device = false;
+  bool repeats = false;
+};
+
+mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos,
+                               const BatchIO& io) {
   auto t0 = std::chrono::steady_clock::now();
   mfs_ctx* c0 = ctxs[0];
   for (int p = 0; p < K; ++p) {
@@ -833,8 +890,9 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     if (s != MFS_OK) return s;
     if (!ctxs[p]->factored) return ctxs[p]->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
     if (ctxs[p]->device != c0->device) return c0->fail(MFS_ERR_ARG, "batched contexts must share one device");
-    for (int q = 0; q < p; ++q)
-      if (ctxs[q] == ctxs[p]) return c0->fail(MFS_ERR_ARG, "a context appears twice in the batch");
+    if (!io.repeats)
+      for (int q = 0; q < p; ++q)
+        if (ctxs[q] == ctxs[p]) return c0->fail(MFS_ERR_ARG, "a context appears twice in the batch");
   }
   if (o.restart < 1 || o.restart + 1 > kMaxBatchVec || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0)
     return c0->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 511])");
@@ -859,8 +917,18 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     }
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
-    launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(),
-               B->wb + B->voff[p], R.st);
+    const size_t bytes = sizeof(double) * 3 * c->P;
+    if (io.v) {
+      const cudaMemcpyKind kind = io.in_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      if (!io.v[p] || !io.w[p]) return c0->fail(MFS_ERR_ARG, "null boundary data in the batch");
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_v + B->boff[p], io.v[p], bytes, kind, R.st));
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_w + B->boff[p], io.w[p], bytes, kind, R.st));
+    } else {
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_v + B->boff[p], c->d_v, bytes, cudaMemcpyDeviceToDevice, R.st));
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_w + B->boff[p], c->d_om, bytes, cudaMemcpyDeviceToDevice, R.st));
+    }
+    launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, B->bc_v + B->boff[p],
+               B->bc_w + B->boff[p], c->bg.data(), B->wb + B->voff[p], R.st);
   }
   CHECK_LAUNCH(c0);
   mfs_status s;
@@ -896,9 +964,10 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     for (int p = 0; p < K; ++p) cyc = std::max(cyc, iters[p] - it_before[p]);
     total_iters += cyc;
     launch_axpy64(n, 1.0, B->e, B->x, R.st);
-    // true residual of every problem with data
+    // true residual of the problems solved in this pass (the others keep theirs; their
+    // segments of r are overwritten with unused values below and never read again)
     std::vector<int> live(K);
-    for (int p = 0; p < K; ++p) live[p] = bnorm[p] > 0;
+    for (int p = 0; p < K; ++p) live[p] = bnorm[p] > 0 && solve_p[p];
     if ((s = set_active(R, live)) != MFS_OK) return s;
     {
       // refinement residual with the native FP64 operator (see mfs_solve)
@@ -931,9 +1000,19 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
   });
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
+    // each context keeps the solution of its last problem in the batch
     CUDA_TRY(c0, cudaMemcpyAsync(c->d_mu, B->x + B->voff[p], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, R.st));
     CUDA_TRY(c0, cudaMemcpyAsync(c->d_lam, B->lam + B->uoff[p], sizeof(double) * c->n_unk, cudaMemcpyDeviceToDevice, R.st));
-    launch_forces_torques(c->src, c->d_lam, c->d_F, c->d_T, R.st);
+    launch_forces_torques(c->src, B->lam + B->uoff[p], B->out_F + B->boff[p], B->out_T + B->boff[p], R.st);
+    const size_t bytes = sizeof(double) * 3 * c->P;
+    CUDA_TRY(c0, cudaMemcpyAsync(c->d_F, B->out_F + B->boff[p], bytes, cudaMemcpyDeviceToDevice, R.st));
+    CUDA_TRY(c0, cudaMemcpyAsync(c->d_T, B->out_T + B->boff[p], bytes, cudaMemcpyDeviceToDevice, R.st));
+    if (io.F && io.F[p])
+      CUDA_TRY(c0, cudaMemcpyAsync(io.F[p], B->out_F + B->boff[p], bytes,
+                                   io.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, R.st));
+    if (io.T && io.T[p])
+      CUDA_TRY(c0, cudaMemcpyAsync(io.T[p], B->out_T + B->boff[p], bytes,
+                                   io.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, R.st));
   }
   CHECK_LAUNCH(c0);
   CUDA_TRY(c0, cudaEventRecord(B->ev, R.st));
@@ -963,10 +1042,11 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
   return first;
 }
 
-mfs_status batch_lockstep(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos) {
+mfs_status batch_lockstep(int K, mfs_ctx* const* ctxs, const mfs_solve_opts& o, mfs_solve_info* infos,
+                          const BatchIO& io = BatchIO()) {
   mfs_ctx* c0 = ctxs[0];
   const long long l0 = launches_on_this_thread();
-  mfs_status s = batch_lockstep_impl(K, ctxs, o, infos);
+  mfs_status s = batch_lockstep_impl(K, ctxs, o, infos, io);
   c0->tm.kernel_launches += launches_on_this_thread() - l0;
   if (c0->prof) {
     cudaStreamSynchronize(c0->stream);
@@ -1845,6 +1925,39 @@ mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve
   for (int i = 0; i < n_problems; ++i)
     if (st[i] != MFS_OK) return st[i];
   return MFS_OK;
+}
+
+static mfs_status batch_rhs_common(int n, mfs_ctx* const* ctxs, const double* const* v, const double* const* omega,
+                                   bool dev, const mfs_solve_opts* opts, mfs_solve_info* infos, double* const* F,
+                                   double* const* T) {
+  if (n < 0 || (n > 0 && (!ctxs || !v || !omega))) return MFS_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return MFS_ERR_ARG;
+  if (n == 0) return MFS_OK;
+  mfs_solve_opts o;
+  if (opts) o = *opts; else mfs_default_solve_opts(&o);
+  if (o.precision != MFS_FP64 && o.precision != MFS_MIXED)
+    return ctxs[0]->fail(MFS_ERR_UNSUPPORTED, "batched right-hand sides support MFS_FP64 and MFS_MIXED");
+  BatchIO io;
+  io.v = v;
+  io.w = omega;
+  io.in_device = dev;
+  io.F = F;
+  io.T = T;
+  io.out_device = dev;
+  io.repeats = true;
+  return batch_lockstep(n, ctxs, o, infos, io);
+}
+
+mfs_status mfs_batch_solve_rhs(int n_problems, mfs_ctx* const* ctxs, const double* const* v, const double* const* omega,
+                               const mfs_solve_opts* opts, mfs_solve_info* infos, double* const* F, double* const* T) {
+  return batch_rhs_common(n_problems, ctxs, v, omega, false, opts, infos, F, T);
+}
+
+mfs_status mfs_batch_solve_rhs_device(int n_problems, mfs_ctx* const* ctxs, const double* const* d_v,
+                                      const double* const* d_omega, const mfs_solve_opts* opts, mfs_solve_info* infos,
+                                      double* const* d_F, double* const* d_T) {
+  return batch_rhs_common(n_problems, ctxs, d_v, d_omega, true, opts, infos, d_F, d_T);
 }
 
 mfs_status mfs_set_profiling(mfs_ctx* c, int on) {

@@ -686,11 +686,11 @@ template <typename T>
 __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, const T* __restrict__ x, T* __restrict__ y) {
   using VT = typename Vec<T>::type;
   constexpr int W = Vec<T>::w;
-  const int job = blockIdx.y;
+  const int job = blockIdx.x;  // jobs sharing a matrix are adjacent, so its rows are read once
   if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = (blockIdx.x * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
+  const int r0 = (blockIdx.y * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
   if (r0 >= nr) return;
   const T* M = B.mat[job];
   const T* xv = x + B.x_off[job];
@@ -729,11 +729,11 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, cons
 template <bool OUT64>
 __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double> B, const float2* __restrict__ x,
                                                                 float2* __restrict__ y2, double* __restrict__ y64) {
-  const int job = blockIdx.y;
+  const int job = blockIdx.x;  // jobs sharing a matrix are adjacent, so its rows are read once
   if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = (blockIdx.x * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
+  const int r0 = (blockIdx.y * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
   if (r0 >= nr) return;
   const float2* M = B.mat_dw[job];
   const float2* xv = x + B.x_off[job];
@@ -864,22 +864,29 @@ __global__ void sub_kernel(int n, const double* __restrict__ a, const double* __
 // ------------------------------------------------------------------ segmented (batched) vector kernels
 constexpr int kSegThreads = 256;
 
-__global__ void seg_dots_kernel(SegTable t, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
-                                double* __restrict__ partial) {
-  const int b = blockIdx.x, i = blockIdx.y;
-  double d = 0.0;
-  if (t.active[t.prob[b]]) {
-    const double* v = V + (long long)i * ldv;
-    for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) d += v[e] * w[e];
-  }
-  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-  __shared__ double red[kSegThreads / 32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+// One CTA per chunk (at most kSegChunkMax elements): the chunk of w is staged in shared memory
+// and each warp forms the partial dot products of its share of the basis vectors.
+constexpr int kSegChunkMax = 1024;
+__global__ void seg_dots_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
+                                const double* __restrict__ w, double* __restrict__ partial) {
+  const int b = blockIdx.x;
+  const bool act = t.active[t.prob[b]] != 0;
+  const long long lo = t.start[b];
+  const int len = (int)(t.end[b] - lo);
+  __shared__ double ws[kSegChunkMax];
+  if (act)
+    for (int e = threadIdx.x; e < len; e += blockDim.x) ws[e] = w[lo + e];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0;
-    for (int q = 0; q < kSegThreads / 32; ++q) s += red[q];
-    partial[(long long)i * t.nchunks + b] = s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int i = warp; i < nvec; i += nwarps) {
+    double d = 0.0;
+    if (act) {
+      const double* v = V + (long long)i * ldv + lo;
+#pragma unroll 4
+      for (int e = lane; e < len; e += 32) d += v[e] * ws[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) partial[(long long)i * t.nchunks + b] = d;
   }
 }
 
@@ -1104,7 +1111,7 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
                      double* h, cudaStream_t st) {
   t_launches += 2;
-  seg_dots_kernel<<<dim3(t.nchunks, nvec), kSegThreads, 0, st>>>(t, V, ldv, w, partial);
+  seg_dots_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, nvec, V, ldv, w, partial);
   seg_reduce_kernel<<<dim3(t.K, nvec), 128, 0, st>>>(t, partial, h);
 }
 void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
@@ -1125,7 +1132,7 @@ template <typename T>
 void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
-  dim3 grid((b.max_rows + rows_per_cta - 1) / rows_per_cta, b.n_jobs);
+  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
   ++t_launches;
   gemv_kernel<T><<<grid, kGemvThreads, 0, st>>>(b, x, y);
 }
@@ -1134,7 +1141,7 @@ template void launch_gemv<float>(const GemvBatch<float>&, const float*, float*, 
 void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, double* y64, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
-  dim3 grid((b.max_rows + rows_per_cta - 1) / rows_per_cta, b.n_jobs);
+  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
   ++t_launches;
   if (y_dw) gemv_dw_kernel<false><<<grid, kGemvThreads, 0, st>>>(b, x, y_dw, nullptr);
   else gemv_dw_kernel<true><<<grid, kGemvThreads, 0, st>>>(b, x, nullptr, y64);

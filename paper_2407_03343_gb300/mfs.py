@@ -104,6 +104,10 @@ def lib():
         "mfs_apply_pairs": (C.c_int, [P, C.c_int, _D, _D, _D]),
         "mfs_apply_precond_noalloc": (C.c_int, [P, P, P]),
         "mfs_batch_solve": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+        "mfs_batch_solve_rhs": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                          C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.POINTER(P), C.POINTER(P)]),
+        "mfs_batch_solve_rhs_device": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                                 C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.POINTER(P), C.POINTER(P)]),
         "mfs_set_profiling": (C.c_int, [P, C.c_int]),
         "mfs_get_timing": (C.c_int, [P, C.POINTER(Timing), C.c_int]),
     }
@@ -319,4 +323,47 @@ def batch_solve(contexts, opts: SolveOpts | None = None, allow_not_converged=Fal
         bad = [i for i in range(n) if infos[i].converged == 0]
         msg = L.mfs_last_error(contexts[bad[0]]._h).decode() if bad else ""
         raise MfsError(st, f"batch solve failed ({len(bad)} problems): {msg}")
+    return list(infos)
+
+
+def batch_solve_rhs(contexts, velocities, opts: SolveOpts | None = None, allow_not_converged=False, **kw):
+    """Several right-hand sides, contexts may repeat: velocities[i] = (v_i, omega_i) host arrays.
+    Returns (infos, [(F_i, T_i)])."""
+    L = lib()
+    n = len(contexts)
+    keep = []
+    vs = (C.c_void_p * n)()
+    ws = (C.c_void_p * n)()
+    Fs = (C.c_void_p * n)()
+    Ts = (C.c_void_p * n)()
+    outs = []
+    for i, (c, (v, w)) in enumerate(zip(contexts, velocities)):
+        v = _f64(v, (c.P, 3))
+        w = _f64(w, (c.P, 3))
+        F = np.zeros((c.P, 3))
+        T = np.zeros((c.P, 3))
+        keep += [v, w]
+        outs.append((F, T))
+        vs[i], ws[i], Fs[i], Ts[i] = v.ctypes.data, w.ctypes.data, F.ctypes.data, T.ctypes.data
+    arr = (C.c_void_p * n)(*[c._h.value for c in contexts])
+    infos = (SolveInfo * n)()
+    o = opts if opts is not None else default_solve_opts(**kw)
+    st = L.mfs_batch_solve_rhs(n, arr, vs, ws, C.byref(o), infos, Fs, Ts)
+    if st != 0 and not (allow_not_converged and st == -5):
+        raise MfsError(st, L.mfs_last_error(contexts[0]._h).decode())
+    return list(infos), outs
+
+
+def batch_solve_rhs_device(contexts, v_ptrs, w_ptrs, F_ptrs, T_ptrs, opts: SolveOpts | None = None,
+                           allow_not_converged=False, **kw):
+    """Device-pointer variant of batch_solve_rhs (pointers as integers)."""
+    L = lib()
+    n = len(contexts)
+    arr = (C.c_void_p * n)(*[c._h.value for c in contexts])
+    infos = (SolveInfo * n)()
+    o = opts if opts is not None else default_solve_opts(**kw)
+    mk = lambda ps: (C.c_void_p * n)(*ps)
+    st = L.mfs_batch_solve_rhs_device(n, arr, mk(v_ptrs), mk(w_ptrs), C.byref(o), infos, mk(F_ptrs), mk(T_ptrs))
+    if st != 0 and not (allow_not_converged and st == -5):
+        raise MfsError(st, L.mfs_last_error(contexts[0]._h).decode())
     return list(infos)
