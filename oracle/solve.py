@@ -347,3 +347,86 @@ def resistance_matrix(disc, system=None):
         F, T = forces_torques(disc, sol.lam)
         Rm[:, j] = np.concatenate([np.concatenate([F[i], T[i]]) for i in range(P)])
     return Rm
+
+
+# ---------------------------------------------------------------- mobility (bordered system)
+#
+# The paper solves the resistance problem and defers the mobility problem (forces and torques
+# given, rigid velocities unknown) to another paper.  Reading used here: the rigid velocities
+# U_k = (V_k, Omega_k) become unknowns of eq. bc, and the force/torque of each sphere, taken
+# from lambda = B^+ mu by the Sec. 2.3 remark, is prescribed:
+#   G_hat mu - W (V_k + Omega_k x (x - c_k)) = -W u_inf(x)          (collocation rows)
+#   s_F F_k(B_k^+ mu_k) = s_F F_k^given,  s_T T_k(B_k^+ mu_k) = s_T T_k^given
+# with s_F = 1/(6 pi mu a), s_T = 1/(8 pi mu a^3) so that the border rows carry velocity scale.
+
+def rigid_block(disc, k) -> np.ndarray:
+    """(3 M_k, 6) matrix of the rigid velocity V + Omega x (x - c_k) at the nodes of sphere k."""
+    sp = disc.spheres[k]
+    r = sp.colloc - sp.centre[None, :]
+    m = r.shape[0]
+    out = np.zeros((m, 3, 6))
+    out[:, :, :3] = np.eye(3)[None, :, :]
+    # Omega x r = [[0, r3, -r2], [-r3, 0, r1], [r2, -r1, 0]] Omega
+    out[:, 0, 4], out[:, 0, 5] = r[:, 2], -r[:, 1]
+    out[:, 1, 3], out[:, 1, 5] = -r[:, 2], r[:, 0]
+    out[:, 2, 3], out[:, 2, 4] = r[:, 1], -r[:, 0]
+    return out.reshape(3 * m, 6)
+
+
+def ft_functional(disc, k) -> np.ndarray:
+    """(6, 3 N_k) matrix taking lambda_k to (F_k, T_k) (Sec. 2.3 remark)."""
+    sp = disc.spheres[k]
+    yS, _, _ = source_sets(disc, k)
+    nS, nI = yS.shape[0], sp.image.shape[0]
+    out = np.zeros((6, n_unknowns(disc, k)))
+    for j in range(nS):
+        out[0:3, 3 * j:3 * j + 3] = np.eye(3)
+        r = yS[j] - sp.centre
+        # (r x f) = [[0, -r3, r2], [r3, 0, -r1], [-r2, r1, 0]] f
+        out[3:6, 3 * j:3 * j + 3] = np.array([[0, -r[2], r[1]], [r[2], 0, -r[0]], [-r[1], r[0], 0]])
+    for j in range(nI):
+        col = 3 * (nS + j)
+        out[3:6, col:col + 3] = np.eye(3)
+    return out
+
+
+class MobilitySystem:
+    """Dense bordered mobility system (reading above), LU-factored once."""
+
+    def __init__(self, disc, op=None):
+        self.disc = disc
+        self.op = op or Operator(disc)
+        P = len(disc.spheres)
+        a, mu_v = disc.radius, disc.params.visc
+        self.sF, self.sT = 1.0 / (6 * math.pi * mu_v * a), 1.0 / (8 * math.pi * mu_v * a ** 3)
+        n = self.op.n
+        A = np.zeros((n + 6 * P, n + 6 * P))
+        A[:n, :n] = self.op.dense()
+        for k in range(P):
+            rows = slice(self.op.roff[k], self.op.roff[k + 1])
+            A[rows, n + 6 * k:n + 6 * k + 6] = -row_scale(disc, k)[:, None] * rigid_block(disc, k)
+            f = self.op.f[k]
+            # FT(B^+ mu_k) with B^+ applied as its two factors
+            ftb = ((ft_functional(disc, k) @ f.V) / f.s[None, :]) @ f.U.T
+            ftb[:3] *= self.sF
+            ftb[3:] *= self.sT
+            A[n + 6 * k:n + 6 * k + 6, rows] = ftb
+        self.A = A
+        self.lu = scipy.linalg.lu_factor(A)
+
+    def solve(self, F, T, background=None):
+        disc, op = self.disc, self.op
+        P = len(disc.spheres)
+        n = op.n
+        b = np.zeros(n + 6 * P)
+        if background is not None:
+            zero = np.zeros((P, 3))
+            # -W u_inf: the boundary data of a fixed sphere in the background flow
+            b[:n] = np.concatenate(rhs(disc, zero, zero, background))
+        for k in range(P):
+            b[n + 6 * k:n + 6 * k + 3] = self.sF * np.asarray(F[k])
+            b[n + 6 * k + 3:n + 6 * k + 6] = self.sT * np.asarray(T[k])
+        x = scipy.linalg.lu_solve(self.lu, b)
+        mu = x[:n]
+        U = x[n:].reshape(P, 6)
+        return U[:, :3].copy(), U[:, 3:].copy(), Solution(lam=op.strengths(mu), mu=mu)
