@@ -138,6 +138,23 @@ mfs_status mfs_set_spheres(mfs_ctx* ctx, int P, const double* centres, const dou
 mfs_status mfs_set_rigid_velocities(mfs_ctx* ctx, const double* v, const double* omega);
 mfs_status mfs_set_rigid_velocities_device(mfs_ctx* ctx, const double* d_v, const double* d_omega);
 
+/* Mobility problem (the inverse of the resistance problem that the Sec. 2.3 remark on forces
+ * and torques makes available): prescribe F (P*3) and T (P*3) on every sphere instead of the
+ * rigid velocities; the next mfs_solve then finds mu together with the velocities V_k, Omega_k
+ * from the bordered system
+ *   G_hat mu - W (V_k + Omega_k x (x - c_k)) = -W u_inf
+ *   s_F F_k(B^+ mu) = s_F F_k,   s_T T_k(B^+ mu) = s_T T_k,
+ * with s_F = 1/(6 pi visc a) and s_T = 1/(8 pi visc a^3) (the single-sphere drag and torque
+ * coefficients, which bring the border rows to the scale of the velocities).  Host arrays,
+ * copied before return; non-finite values give MFS_ERR_ARG.  Requires mfs_build.  The mobility
+ * problem is solved with MFS_FP64 or MFS_MIXED (MFS_FP32 and the batched solves give
+ * MFS_ERR_UNSUPPORTED).  A later mfs_set_rigid_velocities* returns the context to the
+ * resistance problem. */
+mfs_status mfs_set_forces_torques(mfs_ctx* ctx, const double* F, const double* T);
+/* Rigid velocities V (P*3) and Omega (P*3) of the last mobility solve, host arrays;
+ * MFS_ERR_STATE before one. */
+mfs_status mfs_get_rigid_velocities(mfs_ctx* ctx, double* v, double* omega);
+
 /* Background flow u_inf(x) = U + E x + Omega x x subtracted in eq. bc (Sec. 4, Ex. 2).
  * Each pointer may be NULL (term absent): U (3), E (3*3 row-major), Omega (3). */
 mfs_status mfs_set_background_flow(mfs_ctx* ctx, const double* U, const double* E, const double* Omega);

@@ -90,6 +90,10 @@ struct mfs_ctx {
   bool solved = false;
   bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel
   bool factored = false;  // one-body pseudo-inverses available
+  int mode = 0;           // 0: resistance (velocities given), 1: mobility (forces/torques given)
+  int n_sys = 0;          // GMRES system size: n, or n + 6P for the bordered mobility system
+  double* d_border = nullptr;  // mobility: scaled prescribed (F_k, T_k), 6 per sphere
+  double* d_zero = nullptr;    // 3P zeros
   // measurement
   bool prof = false;
   mfs_timing_t tm{};
@@ -298,9 +302,26 @@ void apply_op(mfs_ctx* c, const T* mu, T* out) {
   pairs_step<T>(c, Ops<T>::lh(c), mu, out);
 }
 
+// The GMRES operator: G_hat (resistance), or the bordered mobility operator
+//   [mu; U] -> [G_hat mu - W (V_k + Omega_k x (x - c_k)); s_F F_k(B^+ mu), s_T T_k(B^+ mu)]
+// (forces/torques of lambda_hat = B^+ mu by the Sec. 2.3 remark, s_F = 1/(6 pi mu a),
+// s_T = 1/(8 pi mu a^3)).
+template <typename T>
+void sys_apply(mfs_ctx* c, const T* in, T* out) {
+  apply_op<T>(c, in, out);
+  if constexpr (sizeof(T) == 8) {
+    if (c->mode == 1) {
+      const double a = c->a, mu = c->hd.prm.visc;
+      launch_rigid_sub(c->tg.n, c->d_owner, c->tg.pos64, in + c->n, out, c->stream);
+      launch_forces_torques_scaled(c->src, Ops<T>::lh(c), out + c->n, out + c->n + 3, 6, 1.0 / (6.0 * kPi * mu * a),
+                                   1.0 / (8.0 * kPi * mu * a * a * a), c->stream);
+    }
+  }
+}
+
 template <typename T>
 mfs_status ensure_krylov(mfs_ctx* c, int restart) {
-  size_t need = (size_t)(restart + 1) * (size_t)c->n * sizeof(T);
+  size_t need = (size_t)(restart + 1) * (size_t)c->n_sys * sizeof(T);
   if (c->basis_bytes < need) {
     if (c->d_basis) {
       cudaFree(c->d_basis);
@@ -317,7 +338,7 @@ mfs_status ensure_krylov(mfs_ctx* c, int restart) {
 // dot products of w with V[0..nvec) (FP64 partials) -> host h
 template <typename T>
 mfs_status dots(mfs_ctx* c, int nvec, const T* V, const T* w, double* h_dev) {
-  launch_multidot<T>(c->n, nvec, V, c->n, w, c->d_partial, c->nblk, c->stream);
+  launch_multidot<T>(c->n_sys, nvec, V, c->n_sys, w, c->d_partial, c->nblk, c->stream);
   launch_reduce_partials(nvec, c->nblk, c->d_partial, h_dev, c->stream);
   CHECK_LAUNCH(c);
   return MFS_OK;
@@ -331,7 +352,7 @@ template <typename T>
 mfs_status gmres(mfs_ctx* c, const T* b, T* x, double tol, int restart, int max_iter, int& iters, double& rel) {
   mfs_status s = ensure_krylov<T>(c, restart);
   if (s != MFS_OK) return s;
-  const int n = c->n;
+  const int n = c->n_sys;
   const int ldh = restart + 1;
   T* V = static_cast<T*>(c->d_basis);
   std::vector<double> H((size_t)ldh * restart), cs(restart), sn(restart), g(ldh), hb(2 * ldh + 1), y(restart);
@@ -359,7 +380,7 @@ mfs_status gmres(mfs_ctx* c, const T* b, T* x, double tol, int restart, int max_
       first = false;
     } else {
       // V0 = b - op x
-      apply_op<T>(c, x, V);
+      sys_apply<T>(c, x, V);
       launch_scale_copy<T>(n, V, -1.0, V, c->stream);
       CUDA_TRY(c, cudaMemcpyAsync(coef, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
       launch_update<T>(n, 1, b, n, coef, 1.0, V, c->stream);
@@ -380,7 +401,7 @@ mfs_status gmres(mfs_ctx* c, const T* b, T* x, double tol, int restart, int max_
     bool done = false;
     for (int j = 0; j < restart; ++j) {
       T* w = V + (size_t)(j + 1) * n;
-      apply_op<T>(c, V + (size_t)j * n, w);
+      sys_apply<T>(c, V + (size_t)j * n, w);
       CHECK_LAUNCH(c);
       if ((s = dots<T>(c, j + 1, V, w, h1)) != MFS_OK) return s;
       launch_update<T>(n, j + 1, V, n, h1, -1.0, w, c->stream);
@@ -435,7 +456,7 @@ mfs_status gmres(mfs_ctx* c, const T* b, T* x, double tol, int restart, int max_
 
 // ||v||_2 of an FP64 device vector
 mfs_status norm64(mfs_ctx* c, const double* v, double& out) {
-  mfs_status s = dots<double>(c, 1, v, v, c->d_h + 4 * 512);
+  mfs_status s = dots<double>(c, 1, v, v, c->d_h + 4 * 512);  // over the current system size
   if (s != MFS_OK) return s;
   double r2 = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&r2, c->d_h + 4 * 512, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -889,6 +910,7 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     mfs_status s = check_state(ctxs[p], 2);
     if (s != MFS_OK) return s;
     if (!ctxs[p]->factored) return ctxs[p]->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
+    if (ctxs[p]->mode != 0) return ctxs[p]->fail(MFS_ERR_UNSUPPORTED, "batched solves take rigid velocities");
     if (ctxs[p]->device != c0->device) return c0->fail(MFS_ERR_ARG, "batched contexts must share one device");
     if (!io.repeats)
       for (int q = 0; q < p; ++q)
@@ -1502,10 +1524,13 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   const int n = c->n;
   ALLOC_TRY(c, c->d_v, double, 3 * (size_t)P);
   ALLOC_TRY(c, c->d_om, double, 3 * (size_t)P);
-  ALLOC_TRY(c, c->d_wb, double, n);
-  ALLOC_TRY(c, c->d_mu, double, n);
-  ALLOC_TRY(c, c->d_r, double, n);
-  ALLOC_TRY(c, c->d_w64, double, n);
+  // system vectors hold the 6P border unknowns of the mobility problem as well
+  ALLOC_TRY(c, c->d_wb, double, n + 6 * (size_t)P);
+  ALLOC_TRY(c, c->d_mu, double, n + 6 * (size_t)P);
+  ALLOC_TRY(c, c->d_r, double, n + 6 * (size_t)P);
+  ALLOC_TRY(c, c->d_w64, double, n + 6 * (size_t)P);
+  ALLOC_TRY(c, c->d_border, double, 6 * (size_t)P);
+  ALLOC_TRY(c, c->d_zero, double, 3 * (size_t)P);
   ALLOC_TRY(c, c->d_tmp64, double, c->tmp_len);
   ALLOC_TRY(c, c->d_lh64, double, c->n_unk);
   ALLOC_TRY(c, c->d_lam, double, c->n_unk);
@@ -1522,6 +1547,9 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   ALLOC_TRY(c, c->d_partial, double, (size_t)c->nblk * 512);
   ALLOC_TRY(c, c->d_h, double, 5 * 512);
   CUDA_TRY(c, cudaMemsetAsync(c->d_v, 0, sizeof(double) * 3 * P, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_zero, 0, sizeof(double) * 3 * P, c->stream));
+  c->n_sys = n;
+  c->mode = 0;
   CUDA_TRY(c, cudaMemsetAsync(c->d_om, 0, sizeof(double) * 3 * P, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   {
@@ -1584,6 +1612,7 @@ mfs_status mfs_set_rigid_velocities(mfs_ctx* c, const double* v, const double* o
   CUDA_TRY(c, cudaMemcpyAsync(c->d_v, v, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_om, om, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->mode = 0;
   c->have_bc = true;
   c->solved = false;
   return MFS_OK;
@@ -1595,12 +1624,45 @@ mfs_status mfs_set_rigid_velocities_device(mfs_ctx* c, const double* v, const do
   if (!v || !om) return c->fail(MFS_ERR_ARG, "null velocity array");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_v, v, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_om, om, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  c->mode = 0;
   c->have_bc = true;
   c->solved = false;
   return MFS_OK;
 }
 
 static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info);
+
+mfs_status mfs_set_forces_torques(mfs_ctx* c, const double* F, const double* T) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!F || !T) return c->fail(MFS_ERR_ARG, "null force/torque array");
+  const double a = c->a, mu = c->hd.prm.visc;
+  const double sF = 1.0 / (6.0 * kPi * mu * a), sT = 1.0 / (8.0 * kPi * mu * a * a * a);
+  std::vector<double> b(6 * (size_t)c->P);
+  for (int k = 0; k < c->P; ++k)
+    for (int q = 0; q < 3; ++q) {
+      if (!std::isfinite(F[3 * k + q]) || !std::isfinite(T[3 * k + q])) return c->fail(MFS_ERR_ARG, "non-finite force/torque");
+      b[6 * k + q] = sF * F[3 * k + q];
+      b[6 * k + 3 + q] = sT * T[3 * k + q];
+    }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_border, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->mode = 1;
+  c->have_bc = true;
+  c->solved = false;
+  return MFS_OK;
+}
+
+mfs_status mfs_get_rigid_velocities(mfs_ctx* c, double* v, double* omega) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (!c->solved || c->mode != 1) return c->fail(MFS_ERR_STATE, "no mobility solution yet");
+  if (!v || !omega) return c->fail(MFS_ERR_ARG, "null output");
+  CUDA_TRY(c, cudaMemcpyAsync(v, c->d_v, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(omega, c->d_om, sizeof(double) * 3 * c->P, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return MFS_OK;
+}
 
 mfs_status mfs_solve(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_info* info) {
   const long long l0 = launches_on_this_thread();
@@ -1625,8 +1687,19 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
   if (o.restart < 1 || o.restart > 500 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 ||
       (o.precision != MFS_FP64 && o.precision != MFS_MIXED && o.precision != MFS_FP32))
     return c->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 500])");
-  const int n = c->n;
-  launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(), c->d_wb, c->stream);
+  if (c->mode == 1 && o.precision == MFS_FP32)
+    return c->fail(MFS_ERR_UNSUPPORTED, "the mobility problem is solved in MFS_FP64 or MFS_MIXED");
+  c->n_sys = c->n + (c->mode == 1 ? 6 * c->P : 0);
+  const int n = c->n_sys;
+  if (c->mode == 1) {
+    // fixed spheres in the background flow, plus the prescribed forces and torques
+    launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_zero, c->d_zero, c->bg.data(),
+               c->d_wb, c->stream);
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_wb + c->n, c->d_border, sizeof(double) * 6 * c->P, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    launch_rhs(c->tg.n, c->d_colloc_abs, c->d_owner, c->d_sqrtw, c->src.cen64, c->d_v, c->d_om, c->bg.data(), c->d_wb,
+               c->stream);
+  }
   CHECK_LAUNCH(c);
   double bnorm = 0;
   if ((s = norm64(c, c->d_wb, bnorm)) != MFS_OK) return s;
@@ -1666,7 +1739,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
       // refinement residual with the native FP64 operator: the double-float passes then only
       // have to contract the error, and the final accuracy is that of FP64
       c->dw_pairs = false;
-      apply_op<double>(c, c->d_mu, c->d_w64);
+      sys_apply<double>(c, c->d_mu, c->d_w64);
       c->dw_pairs = (o.precision == MFS_MIXED);
       launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
       CHECK_LAUNCH(c);
@@ -1720,6 +1793,13 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
   // lambda = B^+ mu in FP64, then forces and torques
   precond<double>(c, c->d_mu, c->d_lam);
   launch_forces_torques(c->src, c->d_lam, c->d_F, c->d_T, c->stream);
+  if (c->mode == 1) {
+    // rigid velocities from the border unknowns (V_k, Omega_k) per sphere
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->d_v, 3 * sizeof(double), c->d_mu + c->n, 6 * sizeof(double), 3 * sizeof(double),
+                                  c->P, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->d_om, 3 * sizeof(double), c->d_mu + c->n + 3, 6 * sizeof(double),
+                                  3 * sizeof(double), c->P, cudaMemcpyDeviceToDevice, c->stream));
+  }
   CHECK_LAUNCH(c);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->solved = true;

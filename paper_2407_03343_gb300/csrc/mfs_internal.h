@@ -168,6 +168,11 @@ void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream
 
 // Forces and torques (Sec. 2.3 remark), FP64, one CTA per sphere.
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st);
+// the same with F, T written every `stride` doubles per sphere and scaled by sF, sT
+void launch_forces_torques_scaled(const SourceSet& src, const double* lam, double* F, double* T, int stride, double sF,
+                                  double sT, cudaStream_t st);
+// out[node] -= sqrt(w) (V_k + Omega_k x (x - c_k)), U = (V_k, Omega_k) per sphere, pos64 = targets' (x - c, sqrt w)
+void launch_rigid_sub(int n, const int* owner, const double* pos64, const double* U, double* out, cudaStream_t st);
 // Right-hand side W (v + omega x (x - c) - u_inf(x)), FP64.
 void launch_rhs(int n, const double* colloc_abs, const int* owner, const double* sqrtw, const double* cen,
                 const double* v, const double* om, const double* bg /* 15 doubles: U, E, Omega */,

@@ -953,7 +953,8 @@ __global__ void axpy64_kernel(long long n, double a, const double* __restrict__ 
 // ------------------------------------------------------------------ forces / torques
 __global__ void ft_kernel(int N, const double* __restrict__ proxy64, const double* __restrict__ img64,
                           const int* __restrict__ img_off, const long long* __restrict__ unk_off,
-                          const double* __restrict__ lam, double* __restrict__ F, double* __restrict__ Tq) {
+                          const double* __restrict__ lam, double* __restrict__ F, double* __restrict__ Tq, int stride,
+                          double sF, double sT) {
   const int k = blockIdx.x;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   const double* l = lam + unk_off[k];
@@ -985,7 +986,21 @@ __global__ void ft_kernel(int N, const double* __restrict__ proxy64, const doubl
   if (threadIdx.x < 6) {
     double s = 0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
-    if (threadIdx.x < 3) F[3 * k + threadIdx.x] = s; else Tq[3 * k + threadIdx.x - 3] = s;
+    if (threadIdx.x < 3) F[(long long)stride * k + threadIdx.x] = sF * s;
+    else Tq[(long long)stride * k + threadIdx.x - 3] = sT * s;
+  }
+}
+
+// out[node] -= sqrt(w) (V_k + Omega_k x (x - c_k)) with U = (V_k, Omega_k) per sphere
+__global__ void rigid_sub_kernel(int n, const int* __restrict__ owner, const double* __restrict__ pos64,
+                                 const double* __restrict__ U, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double* u = U + 6LL * owner[i];
+    const double* r = pos64 + 4LL * i;
+    const double sw = r[3];
+    out[3LL * i] -= sw * (u[0] + u[4] * r[2] - u[5] * r[1]);
+    out[3LL * i + 1] -= sw * (u[1] + u[5] * r[0] - u[3] * r[2]);
+    out[3LL * i + 2] -= sw * (u[2] + u[3] * r[1] - u[4] * r[0]);
   }
 }
 
@@ -1203,7 +1218,16 @@ void launch_sub(int n, const double* a, const double* b, double* out, cudaStream
 
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st) {
   ++t_launches;
-  ft_kernel<<<src.P, 256, 0, st>>>(src.N, src.proxy64, src.img64, src.img_off, src.unk_off, lam, F, T);
+  ft_kernel<<<src.P, 256, 0, st>>>(src.N, src.proxy64, src.img64, src.img_off, src.unk_off, lam, F, T, 3, 1.0, 1.0);
+}
+void launch_forces_torques_scaled(const SourceSet& src, const double* lam, double* F, double* T, int stride, double sF,
+                                  double sT, cudaStream_t st) {
+  ++t_launches;
+  ft_kernel<<<src.P, 256, 0, st>>>(src.N, src.proxy64, src.img64, src.img_off, src.unk_off, lam, F, T, stride, sF, sT);
+}
+void launch_rigid_sub(int n, const int* owner, const double* pos64, const double* U, double* out, cudaStream_t st) {
+  ++t_launches;
+  rigid_sub_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, owner, pos64, U, out);
 }
 
 void launch_rhs(int n, const double* colloc_abs, const int* owner, const double* sqrtw, const double* cen,

@@ -89,6 +89,8 @@ def lib():
         "mfs_set_spheres": (C.c_int, [P, C.c_int, _D, _D]),
         "mfs_set_rigid_velocities": (C.c_int, [P, _D, _D]),
         "mfs_set_rigid_velocities_device": (C.c_int, [P, P, P]),
+        "mfs_set_forces_torques": (C.c_int, [P, _D, _D]),
+        "mfs_get_rigid_velocities": (C.c_int, [P, _D, _D]),
         "mfs_set_background_flow": (C.c_int, [P, _D, _D, _D]),
         "mfs_build": (C.c_int, [P, C.POINTER(Params)]),
         "mfs_sizes": (C.c_int, [P, C.POINTER(Sizes)]),
@@ -218,6 +220,19 @@ class Context:
 
     def set_rigid_velocities_device(self, v_ptr: int, omega_ptr: int):
         self._check(self._L.mfs_set_rigid_velocities_device(self._h, C.c_void_p(v_ptr), C.c_void_p(omega_ptr)))
+
+    def set_forces_torques(self, F, T):
+        """Prescribe forces and torques: the next solve is the mobility problem."""
+        F = _f64(F, (self.P, 3))
+        T = _f64(T, (self.P, 3))
+        self._check(self._L.mfs_set_forces_torques(self._h, _dp(F), _dp(T)))
+
+    def rigid_velocities(self):
+        """(V, Omega) found by the last mobility solve, each (P, 3)."""
+        v = np.zeros((self.P, 3))
+        w = np.zeros((self.P, 3))
+        self._check(self._L.mfs_get_rigid_velocities(self._h, _dp(v), _dp(w)))
+        return v, w
 
     def set_background_flow(self, U=None, E=None, Omega=None):
         a = _f64(U, (3,)) if U is not None else None

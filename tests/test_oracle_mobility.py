@@ -50,3 +50,20 @@ def test_squeeze_mobility_inverts_brenner():
     V, W, _ = solve.MobilitySystem(d).solve(F, np.zeros((2, 3)))
     assert np.allclose(V, [[1, 0, 0], [-1, 0, 0]], atol=1e-3)
     assert np.abs(W).max() < 1e-3
+
+
+def test_free_sphere_follows_linear_flow():
+    # Faxen's laws for a force- and torque-free sphere in u_inf = U + E x + w x x:
+    # V = u_inf(c), Omega = w + curl(E x) / 2, with curl(E x)_i = eps_ijk E_kj
+    p = geometry.Params(n_proxy=300, r_proxy=0.7, m_basic=400)
+    c = np.array([0.4, -0.7, 1.1])
+    d = geometry.build([c], 1.0, p)
+    U = np.array([0.2, -0.1, 0.3])
+    E = np.array([[0.1, 1.0, -0.3], [0.2, -0.4, 0.5], [0.0, 0.7, 0.3]])
+    w = np.array([0.3, -0.2, 0.6])
+    bg = solve.Background(U=U, E=E, omega=w)
+    zero = np.zeros((1, 3))
+    V, W, _ = solve.MobilitySystem(d).solve(zero, zero, bg)
+    curl = np.array([E[2, 1] - E[1, 2], E[0, 2] - E[2, 0], E[1, 0] - E[0, 1]])
+    assert np.allclose(V[0], U + E @ c + np.cross(w, c), atol=1e-6)
+    assert np.allclose(W[0], w + 0.5 * curl, atol=1e-6)
