@@ -97,7 +97,20 @@ typedef struct {
   int restart;      /* GMRES restart length m */
   int max_refine;   /* outer refinement steps (MIXED) */
   double inner_tol; /* relative residual reduction asked of each inner solve (MIXED) */
+  int residual;     /* operator of the refinement residual, MFS_RESIDUAL_* below */
 } mfs_solve_opts;
+
+/* Operator that evaluates the refinement residual of MFS_MIXED (MFS_FP64 always uses native FP64,
+ * MFS_FP32 always the FP64 operator as well):
+ *   MFS_RESIDUAL_AUTO   (default) the double-float operator when tol >= MFS_DW_RESIDUAL_MIN_TOL,
+ *                       the native FP64 operator for tighter tolerances;
+ *   MFS_RESIDUAL_FP64   always the native FP64 operator (FP64 pipes, ~70x slower pair sums);
+ *   MFS_RESIDUAL_SOLVE  always the operator of the solve (double-float for MFS_MIXED).
+ * The double-float operator's sums are accurate to ~1e-13 of their absolute sums; the massive
+ * cancellation of the preconditioned operator (lambda_hat ~ 1e9 |mu|) turns that into a residual
+ * floor far below MFS_DW_RESIDUAL_MIN_TOL, so the reported residual stays a faithful measure there. */
+enum { MFS_RESIDUAL_AUTO = 0, MFS_RESIDUAL_FP64 = 1, MFS_RESIDUAL_SOLVE = 2 };
+#define MFS_DW_RESIDUAL_MIN_TOL 5e-7
 
 typedef struct {
   int iters;           /* GMRES iterations (all refinements) */

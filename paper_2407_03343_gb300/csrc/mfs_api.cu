@@ -693,6 +693,14 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   return MFS_OK;
 }
 
+// whether the refinement residual of a solve uses the double-float operator
+static bool dw_residual(const mfs_solve_opts& o) {
+  if (o.precision != MFS_MIXED) return false;
+  if (o.residual == MFS_RESIDUAL_SOLVE) return true;
+  if (o.residual == MFS_RESIDUAL_FP64) return false;
+  return o.tol >= MFS_DW_RESIDUAL_MIN_TOL;
+}
+
 struct BatchRun {
   mfs_ctx* c0;
   BatchPlan* B;
@@ -916,7 +924,8 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
       for (int q = 0; q < p; ++q)
         if (ctxs[q] == ctxs[p]) return c0->fail(MFS_ERR_ARG, "a context appears twice in the batch");
   }
-  if (o.restart < 1 || o.restart + 1 > kMaxBatchVec || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0)
+  if (o.restart < 1 || o.restart + 1 > kMaxBatchVec || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 ||
+      o.residual < MFS_RESIDUAL_AUTO || o.residual > MFS_RESIDUAL_SOLVE)
     return c0->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 511])");
   check_state(c0, 2);
   // reuse the cached plan when the same contexts with the same builds come back
@@ -992,9 +1001,9 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     for (int p = 0; p < K; ++p) live[p] = bnorm[p] > 0 && solve_p[p];
     if ((s = set_active(R, live)) != MFS_OK) return s;
     {
-      // refinement residual with the native FP64 operator (see mfs_solve)
+      // refinement residual with the operator that dw_residual() picks (see mfs_solve)
       const bool dw = R.dw;
-      R.dw = false;
+      R.dw = dw_residual(o);
       batch_apply(R, B->x, B->w);
       R.dw = dw;
     }
@@ -1111,7 +1120,9 @@ void mfs_default_solve_opts(mfs_solve_opts* o) {
   o->restart = 300;
   o->max_refine = 20;
   o->inner_tol = 1e-4;
+  o->residual = MFS_RESIDUAL_AUTO;
 }
+
 
 mfs_status mfs_create(mfs_ctx** out, int device, void* cuda_stream) {
   if (!out) return MFS_ERR_ARG;
@@ -1685,7 +1696,8 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
   mfs_solve_opts o;
   if (opts) o = *opts; else mfs_default_solve_opts(&o);
   if (o.restart < 1 || o.restart > 500 || !(o.tol > 0) || o.max_iter < 1 || o.max_refine < 0 ||
-      (o.precision != MFS_FP64 && o.precision != MFS_MIXED && o.precision != MFS_FP32))
+      (o.precision != MFS_FP64 && o.precision != MFS_MIXED && o.precision != MFS_FP32) ||
+      o.residual < MFS_RESIDUAL_AUTO || o.residual > MFS_RESIDUAL_SOLVE)
     return c->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 500])");
   if (c->mode == 1 && o.precision == MFS_FP32)
     return c->fail(MFS_ERR_UNSUPPORTED, "the mobility problem is solved in MFS_FP64 or MFS_MIXED");
@@ -1736,9 +1748,10 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
         CUDA_TRY(c, cudaMemcpyAsync(c->d_h + 4 * 512 + 8, &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
         launch_update<double>(n, 1, c->d_w64, n, c->d_h + 4 * 512 + 8, 1.0, c->d_mu, c->stream);
       }
-      // refinement residual with the native FP64 operator: the double-float passes then only
-      // have to contract the error, and the final accuracy is that of FP64
-      c->dw_pairs = false;
+      // refinement residual with the native FP64 operator (the double-float passes then only
+      // have to contract the error, and the final accuracy is that of FP64), or, at tolerances
+      // far above its accuracy floor, with the double-float operator
+      c->dw_pairs = dw_residual(o);
       sys_apply<double>(c, c->d_mu, c->d_w64);
       c->dw_pairs = (o.precision == MFS_MIXED);
       launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);

@@ -20,6 +20,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "mfs.h")
 FP64 = 0
 MIXED = 1
 FP32 = 2
+RESIDUAL_AUTO = 0
+RESIDUAL_FP64 = 1
+RESIDUAL_SOLVE = 2
 
 STATUS = {0: "MFS_OK", -1: "MFS_ERR_ARG", -2: "MFS_ERR_GEOMETRY", -3: "MFS_ERR_UNSUPPORTED",
           -4: "MFS_ERR_STATE", -5: "MFS_ERR_NOT_CONVERGED", -6: "MFS_ERR_NUMERIC", -7: "MFS_ERR_OOM",
@@ -37,7 +40,8 @@ class Params(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("precision", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("restart", C.c_int), ("max_refine", C.c_int), ("inner_tol", C.c_double)]
+                ("restart", C.c_int), ("max_refine", C.c_int), ("inner_tol", C.c_double),
+                ("residual", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -157,8 +161,12 @@ def default_solve_opts(**kw) -> SolveOpts:
     o = SolveOpts()
     lib().mfs_default_solve_opts(C.byref(o))
     for k, v in kw.items():
+        if k not in [f[0] for f in SolveOpts._fields_]:
+            raise KeyError(k)
         if k == "precision" and isinstance(v, str):
             v = {"fp64": FP64, "mixed": MIXED, "fp32": FP32}[v]
+        if k == "residual" and isinstance(v, str):
+            v = {"auto": RESIDUAL_AUTO, "fp64": RESIDUAL_FP64, "solve": RESIDUAL_SOLVE}[v]
         setattr(o, k, v)
     return o
 

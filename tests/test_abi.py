@@ -28,6 +28,9 @@ def test_struct_layouts_match_defaults(L):
     assert abs(p.eps_trunc - 5e-12) < 1e-25 and abs(p.nim_a - 8.72) < 1e-15 and abs(p.visc - 1.0) < 1e-15
     o = mfs.default_solve_opts()
     assert o.precision == mfs.MIXED and abs(o.tol - 1e-6) < 1e-20 and o.restart == 300
+    assert o.max_iter == 2000 and o.max_refine == 20 and o.residual == mfs.RESIDUAL_AUTO
+    with pytest.raises(KeyError):
+        mfs.default_solve_opts(tolerance=1e-3)
 
 
 def test_null_context_is_rejected_without_gpu(L):
