@@ -93,6 +93,7 @@ struct mfs_ctx {
   int mode = 0;           // 0: resistance (velocities given), 1: mobility (forces/torques given)
   int n_sys = 0;          // GMRES system size: n, or n + 6P for the bordered mobility system
   double* d_border = nullptr;  // mobility: scaled prescribed (F_k, T_k), 6 per sphere
+  double* d_pparts = nullptr;  // partial sums of the source-split pair kernel, kPairMaxParts * n
   double* d_zero = nullptr;    // 3P zeros
   // measurement
   bool prof = false;
@@ -277,7 +278,7 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
   timed(c, c->ev_pair, [&] {
     if constexpr (sizeof(T) == 8) {
       if (c->dw_pairs) {
-        launch_pairs_dw(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->stream);
+        launch_pairs_dw(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream);
         return;
       }
     }
@@ -490,6 +491,14 @@ struct BatchPlan {
   int2* d_work1 = nullptr;
   int n_work = 0, n_work1 = 0;
   std::vector<int> tiles4;   // large tiles per problem, to pick the tiling of each launch
+  std::vector<int> tiles1;
+  std::vector<long long> others_p;  // proxies of the other spheres per problem (source split)
+  std::vector<int2> w4_host, w1_host;  // full work lists; the launches use the active problems' part
+  int2* d_cwork = nullptr;   // compacted (problem, tile) lists of the active problems
+  int2* d_cwork1 = nullptr;
+  int2* wpin = nullptr;      // pinned staging for them
+  int n_cwork = 0, n_cwork1 = 0;
+  double* pparts = nullptr;  // source-split partial sums, kPairMaxParts * n_total
   int* d_active = nullptr;
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
@@ -509,6 +518,7 @@ struct BatchPlan {
     if (basis) cudaFree(basis);
     if (hpin) cudaFreeHost(hpin);
     if (apin) cudaFreeHost(apin);
+    if (wpin) cudaFreeHost(wpin);
     if (ev) cudaEventDestroy(ev);
   }
   template <typename T>
@@ -570,7 +580,11 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
     for (int t = 0; t < c->tg.n_tiles; ++t) work4.push_back(make_int2(p, t));
     for (int t = 0; t < c->tg.n_tiles1; ++t) work1.push_back(make_int2(p, t));
     B->tiles4.push_back(c->tg.n_tiles);
+    B->tiles1.push_back(c->tg.n_tiles1);
+    B->others_p.push_back((long long)(c->P - 1) * c->src.N);
   }
+  B->w4_host = work4;
+  B->w1_host = work1;
   B->n_work = (int)work4.size();
   B->n_work1 = (int)work1.size();
   B->d_args = B->alloc<char>(args4.size());
@@ -581,7 +595,10 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   ok = ok && put(B, B->d_work, work4) && put(B, B->d_work1, work1) && put(B, B->d_uoff, B->uoff) &&
        put(B, B->d_voff, B->voff);
   B->d_active = B->alloc<int>(K);
-  ok = ok && B->d_active;
+  B->d_cwork = B->alloc<int2>(work4.size());
+  B->d_cwork1 = B->alloc<int2>(work1.size());
+  ok = ok && B->d_active && B->d_cwork && B->d_cwork1 &&
+       cudaMallocHost(&B->wpin, sizeof(int2) * std::max<size_t>(1, work4.size() + work1.size())) == cudaSuccess;
   // GEMV jobs: every sphere of every problem, with the problems that share a context (several
   // right-hand sides on one geometry) adjacent, so a factor matrix is read once for all of them
   std::vector<const double*> mA, mV;
@@ -677,7 +694,8 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
        (B->partial = B->alloc<double>((size_t)kMaxBatchVec * B->seg.nchunks)) &&
        (B->hbuf = B->alloc<double>((size_t)(2 * kMaxBatchVec + 1) * K)) &&
        (B->coef = B->alloc<double>((size_t)kMaxBatchVec * K)) && (B->scl = B->alloc<double>(K)) &&
-       (B->x2 = B->alloc<float2>(n)) && (B->t2 = B->alloc<float2>(B->t_total));
+       (B->x2 = B->alloc<float2>(n)) && (B->t2 = B->alloc<float2>(B->t_total)) &&
+       (B->pparts = B->alloc<double>((size_t)kPairMaxParts * n));
   B->boff.assign(K + 1, 0);
   for (int p = 0; p < K; ++p) B->boff[p + 1] = B->boff[p] + 3LL * ctxs[p]->P;
   ok = ok && (B->bc_v = B->alloc<double>(B->boff[K])) && (B->bc_w = B->alloc<double>(B->boff[K])) &&
@@ -709,11 +727,25 @@ struct BatchRun {
   std::vector<int> act;  // host copy of the active flags
 };
 
+// Active flags and the compacted pair work lists of the active problems.
 mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
+  BatchPlan* B = R.B;
+  if (!R.act.empty() && R.act == a) return MFS_OK;
   R.act = a;
-  for (int p = 0; p < R.B->K; ++p) R.B->apin[p] = a[p];
-  CUDA_TRY(R.c0, cudaMemcpyAsync(R.B->d_active, R.B->apin, sizeof(int) * R.B->K, cudaMemcpyHostToDevice, R.st));
-  // the pinned staging buffer is rewritten by the next call: wait for this copy
+  for (int p = 0; p < B->K; ++p) B->apin[p] = a[p];
+  int n4 = 0, n1 = 0;
+  int2* w4 = B->wpin;
+  int2* w1 = B->wpin + B->w4_host.size();
+  for (const int2& w : B->w4_host)
+    if (a[w.x]) w4[n4++] = w;
+  for (const int2& w : B->w1_host)
+    if (a[w.x]) w1[n1++] = w;
+  B->n_cwork = n4;
+  B->n_cwork1 = n1;
+  CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_active, B->apin, sizeof(int) * B->K, cudaMemcpyHostToDevice, R.st));
+  if (n4) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork, w4, sizeof(int2) * n4, cudaMemcpyHostToDevice, R.st));
+  if (n1) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork1, w1, sizeof(int2) * n1, cudaMemcpyHostToDevice, R.st));
+  // the pinned staging buffers are rewritten by the next call: wait for these copies
   CUDA_TRY(R.c0, cudaStreamSynchronize(R.st));
   return MFS_OK;
 }
@@ -732,17 +764,22 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
       launch_gemv<double>(B->gV, B->tmp, B->lh, R.st);
     }
   });
-  long long active_tiles = 0;
+  long long active_tiles = 0, min_others = -1;
   for (int p = 0; p < B->K; ++p)
-    if (R.act[p]) active_tiles += B->tiles4[p];
+    if (R.act[p]) {
+      active_tiles += B->tiles4[p];
+      if (B->others_p[p] > 0) min_others = min_others < 0 ? B->others_p[p] : std::min(min_others, B->others_p[p]);
+    }
   const int nt = pair_nodes_per_thread((int)std::min<long long>(active_tiles, 1 << 30));
+  // few tiles left (the lockstep tail): split each tile's sources over several CTAs
+  const int parts = R.dw && nt == 1 && min_others > 0 ? pair_split_parts(B->n_cwork1, min_others, kPairMaxParts) : 1;
   timed(c, c->ev_pair, [&] {
     if (nt == 4)
-      launch_pairs_batch64(R.dw, B->d_args, B->d_work, B->n_work, B->d_active, 4, B->lh, in, out, B->d_uoff,
-                           B->d_voff, R.st);
+      launch_pairs_batch64(R.dw, B->d_args, B->d_cwork, B->n_cwork, B->d_active, 4, B->lh, in, out, B->d_uoff,
+                           B->d_voff, 1, nullptr, 0, B->seg, R.st);
     else
-      launch_pairs_batch64(R.dw, B->d_args1, B->d_work1, B->n_work1, B->d_active, 1, B->lh, in, out, B->d_uoff,
-                           B->d_voff, R.st);
+      launch_pairs_batch64(R.dw, B->d_args1, B->d_cwork1, B->n_cwork1, B->d_active, 1, B->lh, in, out, B->d_uoff,
+                           B->d_voff, parts, B->pparts, B->n_total, B->seg, R.st);
   });
   c->tm.gemv_launches += 2;
   c->tm.pair_launches += 1;
@@ -939,7 +976,7 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     if (s != MFS_OK) return s;
     c0->batch = B;
   }
-  BatchRun R{c0, B, c0->stream, o.precision == MFS_MIXED, std::vector<int>(K, 1)};
+  BatchRun R{c0, B, c0->stream, o.precision == MFS_MIXED, std::vector<int>()};  // act empty: the first set_active uploads
   // order after the work already queued on every context's stream
   for (int p = 0; p < K; ++p)
     if (ctxs[p]->stream != R.st) {
@@ -1542,6 +1579,7 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   ALLOC_TRY(c, c->d_w64, double, n + 6 * (size_t)P);
   ALLOC_TRY(c, c->d_border, double, 6 * (size_t)P);
   ALLOC_TRY(c, c->d_zero, double, 3 * (size_t)P);
+  ALLOC_TRY(c, c->d_pparts, double, (size_t)kPairMaxParts * n);
   ALLOC_TRY(c, c->d_tmp64, double, c->tmp_len);
   ALLOC_TRY(c, c->d_lh64, double, c->n_unk);
   ALLOC_TRY(c, c->d_lam, double, c->n_unk);

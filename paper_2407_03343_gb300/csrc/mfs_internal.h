@@ -91,18 +91,31 @@ void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, c
                   T* out, double visc, cudaStream_t st);
 
 // Same sums as launch_pairs<double> (FP64 in and out) computed in double-float arithmetic on
-// the FP32 pipes.
+// the FP32 pipes.  With few target tiles the sources of each tile are split over up to
+// max_parts CTAs whose partial sums go to `partial` (max_parts * 3 n doubles; null: no split)
+// and are added in a second, deterministic pass.
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu,
-                     double* out, double visc, cudaStream_t st);
+                     double* out, double visc, double* partial, int max_parts, cudaStream_t st);
+// Source split of the 1-node-per-thread tiling: as many parts as keep the CTAs within one wave
+// (152 SMs x 7 resident CTAs of the double-float kernel: 72 registers x 128 threads, 28 KB of
+// shared memory), at least kPairSplitMinSources sources per part, at most max_parts.
+constexpr int kPairSplitTarget = 152 * 7;
+constexpr int kPairSplitMinSources = 64;
+constexpr int kPairMaxParts = 16;
+int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts);
 
 // Many problems per launch (FP64 data): a device table of per-problem kernel arguments, a work
 // list of (problem, tile) pairs and a per-problem active flag.
 size_t pair_args64_bytes();
 void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src, const double* lam_hat,
                       const double* mu, double* out, double visc, int nodes_per_thread);
+struct SegTable;
+// parts > 1 (double-float, 1 node per thread only): sources split as in launch_pairs_dw, the
+// partial sums in `partial` (parts slices of pstride doubles) reduced over the chunks of `seg`.
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
-                          const long long* d_uoff, const long long* d_voff, cudaStream_t st);
+                          const long long* d_uoff, const long long* d_voff, int parts, double* partial,
+                          long long pstride, const SegTable& seg, cudaStream_t st);
 
 // Batched GEMV: for every job j, y_j = M_j x_j with M_j row-major (rows_j x cols_j, leading dim ld_j).
 template <typename T>

@@ -441,8 +441,13 @@ struct __align__(16) DWPos {
   float xl, yl, zl, pad1;
 };
 
+// Sources may be split over `nparts` CTAs per target tile (when there are too few tiles to
+// fill the GPU): part `part` takes a contiguous share of the tile's source list (the sources of
+// every other sphere) and, for nparts > 1, writes its scaled partial sum to
+// partial[part * pstride + 3 node + c] for pair_parts_reduce to finish.
 template <int NT>
-__device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const int t) {
+__device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const int t, const int part, const int nparts,
+                                             double* __restrict__ partial, const long long pstride) {
   __shared__ float4 sp[2 * kTileProxy];   // position hi, lo
   __shared__ float4 sf[2 * kTileProxy];   // strength hi, lo
   __shared__ float4 si[6 * kTileImg];     // image node: 12 hi values (3 float4), then 12 lo values (3 float4)
@@ -468,10 +473,14 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
   const double far = 1e18;
 
   const int total = A.P * A.N;
-  // the proxies before and after sphere k's own, in tiles with exact trip counts
+  // the proxies before and after sphere k's own (this part's share of them), in tiles with
+  // exact trip counts
+  const int p_lo = k < 0 ? total : k * A.N, p_w = k < 0 ? 0 : A.N;
+  const long long p_eff = total - p_w;
+  const int pe0 = (int)(p_eff * part / nparts), pe1 = (int)(p_eff * (part + 1) / nparts);
   for (int rr = 0; rr < 2; ++rr) {
-  const int r_lo = rr == 0 ? 0 : (k < 0 ? total : (k + 1) * A.N);
-  const int r_hi = rr == 0 ? (k < 0 ? total : k * A.N) : total;
+  const int r_lo = rr == 0 ? min(pe0, p_lo) : max(pe0, p_lo) + p_w;
+  const int r_hi = rr == 0 ? min(pe1, p_lo) : max(pe1, p_lo) + p_w;
   for (int s0 = r_lo; s0 < r_hi; s0 += kTileProxy) {
     const int ns = min(kTileProxy, r_hi - s0);
     __syncthreads();
@@ -524,10 +533,13 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
   }
   }
 
-  const int self_lo = k >= 0 ? A.img_off[k] : 0, self_hi = k >= 0 ? A.img_off[k + 1] : 0;
+  // image nodes before and after sphere k's own, this part's share
+  const int i_lo = k >= 0 ? A.img_off[k] : 0, i_w = k >= 0 ? A.img_off[k + 1] - i_lo : 0;
+  const long long i_eff = A.n_img - i_w;
+  const int ie0 = (int)(i_eff * part / nparts), ie1 = (int)(i_eff * (part + 1) / nparts);
   for (int rr = 0; rr < 2; ++rr) {
-  const int r_lo = rr == 0 ? 0 : self_hi;
-  const int r_hi = rr == 0 ? self_lo : A.n_img;
+  const int r_lo = rr == 0 ? min(ie0, i_lo) : max(ie0, i_lo) + i_w;
+  const int r_hi = rr == 0 ? min(ie1, i_lo) : max(ie1, i_lo) + i_w;
   for (int s0 = r_lo; s0 < r_hi; s0 += kTileImg) {
     const int ns = min(kTileImg, r_hi - s0);
     __syncthreads();
@@ -609,7 +621,12 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       long long node = start + idx;
       double sw = A.tgt[node].w;
       double gx = dw_join(ux[q]) * A.scale, gy = dw_join(uy[q]) * A.scale, gz = dw_join(uz[q]) * A.scale;
-      if (A.mu) {
+      if (nparts > 1) {
+        double* o = partial + part * pstride + 3 * node;
+        o[0] = gx;
+        o[1] = gy;
+        o[2] = gz;
+      } else if (A.mu) {
         A.out[3 * node] = A.mu[3 * node] + sw * gx;
         A.out[3 * node + 1] = A.mu[3 * node + 1] + sw * gy;
         A.out[3 * node + 2] = A.mu[3 * node + 2] + sw * gz;
@@ -627,8 +644,19 @@ __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
   pair_tile<T, NT>(A, blockIdx.x);
 }
 template <int NT>
-__global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A) {
-  pair_tile_dw<NT>(A, blockIdx.x);
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A, int nparts, double* partial,
+                                                                long long pstride) {
+  pair_tile_dw<NT>(A, blockIdx.x / nparts, blockIdx.x % nparts, nparts, partial, pstride);
+}
+// out = mu + sqrt(w) * (sum of the parts), or the plain sum when mu is null; parts added in order
+__global__ void pair_parts_reduce_kernel(long long n3, const D4* __restrict__ tgt, int nparts,
+                                         const double* __restrict__ partial, long long pstride,
+                                         const double* __restrict__ mu, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += partial[q * pstride + e];
+    out[e] = mu ? mu[e] + tgt[e / 3].w * s : s;
+  }
 }
 // Many problems in one launch: work[b] = (problem, tile); problems whose flag is 0 are skipped.
 // The per-problem vectors are segments of concatenated ones: lam at lam + uoff[p], mu and out
@@ -639,6 +667,8 @@ struct BatchVecs {
   double* out;
   const long long* uoff;
   const long long* voff;
+  double* partial;     // split sources: nparts slices of the concatenated vector length
+  long long pstride;
 };
 template <typename T, int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArgs<T>* __restrict__ args,
@@ -655,14 +685,29 @@ __global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArg
 template <int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const PairArgs<double>* __restrict__ args,
                                                                       const int2* __restrict__ work,
-                                                                      const int* __restrict__ active, BatchVecs bv) {
-  const int2 w = work[blockIdx.x];
+                                                                      const int* __restrict__ active, BatchVecs bv,
+                                                                      int nparts) {
+  const int2 w = work[blockIdx.x / nparts];
   if (!active[w.x]) return;
   PairArgs<double> A = args[w.x];
   A.lam = bv.lam + bv.uoff[w.x];
   A.mu = bv.mu + bv.voff[w.x];
   A.out = bv.out + bv.voff[w.x];
-  pair_tile_dw<NT>(A, w.y);
+  pair_tile_dw<NT>(A, w.y, blockIdx.x % nparts, nparts, bv.partial + bv.voff[w.x], bv.pstride);
+}
+// the batched counterpart of pair_parts_reduce_kernel, one CTA per vector chunk of an active problem
+__global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double>* __restrict__ args, BatchVecs bv,
+                                               int nparts) {
+  const int b = blockIdx.x;
+  const int p = t.prob[b];
+  if (!t.active[p]) return;
+  const D4* tgt = args[p].tgt;
+  const long long base = bv.voff[p];
+  for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += bv.partial[q * bv.pstride + e];
+    bv.out[e] = bv.mu[e] + tgt[(e - base) / 3].w * s;
+  }
 }
 
 // ------------------------------------------------------------------ batched GEMV
@@ -1089,14 +1134,31 @@ void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, c
 template void launch_pairs<float>(const TargetSet&, const SourceSet&, const float*, const float*, float*, double, cudaStream_t);
 template void launch_pairs<double>(const TargetSet&, const SourceSet&, const double*, const double*, double*, double, cudaStream_t);
 
+int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts) {
+  if (n_tiles1 <= 0) return 1;
+  long long s = kPairSplitTarget / n_tiles1;  // at most one wave of resident CTAs
+  s = std::min<long long>(s, min_sources / kPairSplitMinSources);
+  s = std::min<long long>(s, max_parts);
+  return (int)std::max<long long>(s, 1);
+}
+
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu, double* out,
-                     double visc, cudaStream_t st) {
+                     double visc, double* partial, int max_parts, cudaStream_t st) {
   if (tg.n_tiles == 0) return;
   const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
   PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
   ++t_launches;
-  if (nt == 4) pairs_dw_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
-  else pairs_dw_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A);
+  if (nt == 4) {
+    pairs_dw_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A, 1, nullptr, 0);
+    return;
+  }
+  const int parts = partial ? pair_split_parts(tg.n_tiles1, (long long)(src.P - 1) * src.N, max_parts) : 1;
+  const long long n3 = 3LL * tg.n;
+  pairs_dw_kernel<1><<<tg.n_tiles1 * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  if (parts > 1) {
+    ++t_launches;
+    pair_parts_reduce_kernel<<<grid_for(n3, 256), 256, 0, st>>>(n3, A.tgt, parts, partial, n3, mu, out);
+  }
 }
 
 size_t pair_args64_bytes() { return sizeof(PairArgs<double>); }
@@ -1109,14 +1171,23 @@ void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src,
 
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
-                          const long long* d_uoff, const long long* d_voff, cudaStream_t st) {
+                          const long long* d_uoff, const long long* d_voff, int parts, double* partial,
+                          long long pstride, const SegTable& seg, cudaStream_t st) {
   if (n_work == 0) return;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args);
-  BatchVecs bv{lam, mu, out, d_uoff, d_voff};
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride};
   ++t_launches;
   if (double_float) {
-    if (nodes_per_thread == 4) pairs_dw_batch_kernel<4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
-    else pairs_dw_batch_kernel<1><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
+    if (nodes_per_thread == 4) {
+      pairs_dw_batch_kernel<4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv, 1);
+    } else {
+      if (!partial) parts = 1;
+      pairs_dw_batch_kernel<1><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_active, bv, parts);
+      if (parts > 1) {
+        ++t_launches;
+        pair_parts_reduce_batch_kernel<<<seg.nchunks, 256, 0, st>>>(seg, args, bv, parts);
+      }
+    }
   } else {
     if (nodes_per_thread == 4) pairs_batch_kernel<double, 4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
     else pairs_batch_kernel<double, 1><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
