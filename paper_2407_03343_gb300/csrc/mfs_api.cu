@@ -499,6 +499,9 @@ struct BatchPlan {
   int2* wpin = nullptr;      // pinned staging for them
   int n_cwork = 0, n_cwork1 = 0;
   double* pparts = nullptr;  // source-split partial sums, kPairMaxParts * n_total
+  std::vector<int> cprob_host;  // problem of each vector chunk
+  int* d_cchunk = nullptr;      // compacted chunk list of the active problems (seg.list)
+  int* cpin = nullptr;          // pinned staging for it
   int* d_active = nullptr;
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
@@ -519,6 +522,7 @@ struct BatchPlan {
     if (hpin) cudaFreeHost(hpin);
     if (apin) cudaFreeHost(apin);
     if (wpin) cudaFreeHost(wpin);
+    if (cpin) cudaFreeHost(cpin);
     if (ev) cudaEventDestroy(ev);
   }
   template <typename T>
@@ -677,7 +681,9 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   }
   int *dcp = nullptr, *dpc = nullptr;
   long long *dcs = nullptr, *dce = nullptr;
-  ok = ok && put(B, dcp, cprob) && put(B, dpc, pchunk) && put(B, dcs, cs) && put(B, dce, ce);
+  B->cprob_host = cprob;
+  ok = ok && put(B, dcp, cprob) && put(B, dpc, pchunk) && put(B, dcs, cs) && put(B, dce, ce) &&
+       (B->d_cchunk = B->alloc<int>(cprob.size()));
   if (ok) {
     B->seg.K = K;
     B->seg.nchunks = (int)cprob.size();
@@ -686,6 +692,8 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
     B->seg.end = dce;
     B->seg.pchunk = dpc;
     B->seg.active = B->d_active;
+    B->seg.list = B->d_cchunk;
+    B->seg.nlist = 0;
   }
   const long long n = B->n_total;
   ok = ok && (B->wb = B->alloc<double>(n)) && (B->x = B->alloc<double>(n)) && (B->r = B->alloc<double>(n)) &&
@@ -701,7 +709,9 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   ok = ok && (B->bc_v = B->alloc<double>(B->boff[K])) && (B->bc_w = B->alloc<double>(B->boff[K])) &&
        (B->out_F = B->alloc<double>(B->boff[K])) && (B->out_T = B->alloc<double>(B->boff[K]));
   ok = ok && cudaMallocHost(&B->hpin, sizeof(double) * (2 * kMaxBatchVec + 1) * K) == cudaSuccess &&
-       cudaMallocHost(&B->apin, sizeof(int) * K) == cudaSuccess && cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming) == cudaSuccess;
+       cudaMallocHost(&B->apin, sizeof(int) * K) == cudaSuccess &&
+       cudaMallocHost(&B->cpin, sizeof(int) * std::max<size_t>(1, B->cprob_host.size())) == cudaSuccess &&
+       cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     delete B;
@@ -742,7 +752,12 @@ mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
     if (a[w.x]) w1[n1++] = w;
   B->n_cwork = n4;
   B->n_cwork1 = n1;
+  int nc = 0;
+  for (int b = 0; b < (int)B->cprob_host.size(); ++b)
+    if (a[B->cprob_host[b]]) B->cpin[nc++] = b;
+  B->seg.nlist = nc;
   CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_active, B->apin, sizeof(int) * B->K, cudaMemcpyHostToDevice, R.st));
+  if (nc) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cchunk, B->cpin, sizeof(int) * nc, cudaMemcpyHostToDevice, R.st));
   if (n4) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork, w4, sizeof(int2) * n4, cudaMemcpyHostToDevice, R.st));
   if (n1) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork1, w1, sizeof(int2) * n1, cudaMemcpyHostToDevice, R.st));
   // the pinned staging buffers are rewritten by the next call: wait for these copies

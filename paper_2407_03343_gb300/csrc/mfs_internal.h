@@ -171,6 +171,8 @@ struct SegTable {
   const long long* end = nullptr;
   const int* pchunk = nullptr;  // K+1 chunk offsets per problem
   const int* active = nullptr;
+  const int* list = nullptr;    // optional: the chunks of the active problems (nlist of them); the
+  int nlist = 0;                //   launches then cover only those
 };
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
                      double* h, cudaStream_t st);

@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const Pair
 // the batched counterpart of pair_parts_reduce_kernel, one CTA per vector chunk of an active problem
 __global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double>* __restrict__ args, BatchVecs bv,
                                                int nparts) {
-  const int b = blockIdx.x;
+  const int b = t.list ? t.list[blockIdx.x] : blockIdx.x;
   const int p = t.prob[b];
   if (!t.active[p]) return;
   const D4* tgt = args[p].tgt;
@@ -909,81 +909,71 @@ __global__ void sub_kernel(int n, const double* __restrict__ a, const double* __
 // ------------------------------------------------------------------ segmented (batched) vector kernels
 constexpr int kSegThreads = 256;
 
-// One CTA per chunk (at most kSegChunkMax elements): the chunk of w is staged in shared memory
-// and each warp forms the partial dot products of its share of the basis vectors.
+// The chunk a CTA works on: blockIdx.x indexes the compacted list of the active problems'
+// chunks when the table carries one, else all chunks (inactive ones return at once).
+__device__ __forceinline__ int seg_chunk(const SegTable& t) { return t.list ? t.list[blockIdx.x] : blockIdx.x; }
+
+// Partial dot products of w with basis vectors over one chunk: CTA (chunk, vector block) stages
+// the chunk of w (at most kSegChunkMax elements) in shared memory and each warp takes vectors of
+// its block, so the launch has enough CTAs to keep HBM busy even for a single short problem.
 constexpr int kSegChunkMax = 1024;
+constexpr int kSegDotVecs = 16;   // basis vectors per CTA
+constexpr int kSegUpdSub = 128;   // elements per CTA of the update (one per thread)
 __global__ void seg_dots_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
                                 const double* __restrict__ w, double* __restrict__ partial) {
-  const int b = blockIdx.x;
-  const bool act = t.active[t.prob[b]] != 0;
+  const int b = seg_chunk(t);
+  if (!t.active[t.prob[b]]) return;
   const long long lo = t.start[b];
   const int len = (int)(t.end[b] - lo);
   __shared__ double ws[kSegChunkMax];
-  if (act)
-    for (int e = threadIdx.x; e < len; e += blockDim.x) ws[e] = w[lo + e];
+  for (int e = threadIdx.x; e < len; e += blockDim.x) ws[e] = w[lo + e];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int i = warp; i < nvec; i += nwarps) {
+  const int i1 = min(nvec, (int)(blockIdx.y + 1) * kSegDotVecs);
+  for (int i = blockIdx.y * kSegDotVecs + warp; i < i1; i += nwarps) {
+    const double* v = V + (long long)i * ldv + lo;
     double d = 0.0;
-    if (act) {
-      const double* v = V + (long long)i * ldv + lo;
-#pragma unroll 4
-      for (int e = lane; e < len; e += 32) d += v[e] * ws[e];
-    }
+#pragma unroll 8
+    for (int e = lane; e < len; e += 32) d += v[e] * ws[e];
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if (lane == 0) partial[(long long)i * t.nchunks + b] = d;
   }
 }
 
-__global__ void seg_reduce_kernel(SegTable t, const double* __restrict__ partial, double* __restrict__ h) {
-  const int p = blockIdx.x, i = blockIdx.y;
-  double s = 0.0;
-  for (int b = t.pchunk[p] + threadIdx.x; b < t.pchunk[p + 1]; b += blockDim.x) s += partial[(long long)i * t.nchunks + b];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += red[q];
-    h[(long long)i * t.K + p] = r;
+// h[i K + p] = sum over problem p's chunks (in order) of the partial dots of vector i
+__global__ void seg_reduce_kernel(SegTable t, int nvec, const double* __restrict__ partial, double* __restrict__ h) {
+  const int p = blockIdx.x;
+  if (!t.active[p]) return;
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = t.pchunk[p]; b < t.pchunk[p + 1]; ++b) s += partial[(long long)i * t.nchunks + b];
+    h[(long long)i * t.K + p] = s;
   }
 }
 
+// w += sign * sum_i coef[i K + p] V_i over one kSegUpdSub-element piece of a chunk per CTA
 __global__ void seg_update_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
                                   const double* __restrict__ coef, double sign, double* __restrict__ w) {
-  const int b = blockIdx.x;
+  const int b = seg_chunk(t);
   const int p = t.prob[b];
   if (!t.active[p]) return;
+  const long long e = t.start[b] + (long long)blockIdx.y * kSegUpdSub + threadIdx.x;
+  if (t.start[b] + (long long)blockIdx.y * kSegUpdSub >= t.end[b]) return;  // whole CTA past the chunk
   __shared__ double c[512];
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) c[i] = sign * coef[(long long)i * t.K + p];
   __syncthreads();
-  // four elements per thread with independent accumulators keep several basis loads in flight
-  const long long lo = t.start[b], hi = t.end[b];
-  const int step = blockDim.x;
-  for (long long e0 = lo + threadIdx.x; e0 < hi; e0 += 4LL * step) {
-    const long long e1 = e0 + step, e2 = e0 + 2LL * step, e3 = e0 + 3LL * step;
-    const bool v1 = e1 < hi, v2 = e2 < hi, v3 = e3 < hi;
-    double a0 = w[e0], a1 = v1 ? w[e1] : 0.0, a2 = v2 ? w[e2] : 0.0, a3 = v3 ? w[e3] : 0.0;
-#pragma unroll 4
-    for (int i = 0; i < nvec; ++i) {
-      const double* vi = V + (long long)i * ldv;
-      const double ci = c[i];
-      a0 += ci * vi[e0];
-      if (v1) a1 += ci * vi[e1];
-      if (v2) a2 += ci * vi[e2];
-      if (v3) a3 += ci * vi[e3];
-    }
-    w[e0] = a0;
-    if (v1) w[e1] = a1;
-    if (v2) w[e2] = a2;
-    if (v3) w[e3] = a3;
-  }
+  if (e >= t.end[b]) return;
+  double a = w[e];
+#pragma unroll 8
+  for (int i = 0; i < nvec; ++i) a += c[i] * V[(long long)i * ldv + e];
+  w[e] = a;
 }
+
+inline int seg_ctas(const SegTable& t) { return t.list ? t.nlist : t.nchunks; }
 
 __global__ void seg_scale_kernel(SegTable t, const double* __restrict__ s, const double* __restrict__ in,
                                  double* __restrict__ out) {
-  const int b = blockIdx.x;
+  const int b = seg_chunk(t);
   const int p = t.prob[b];
   if (!t.active[p]) return;
   const double f = s[p];
@@ -1185,7 +1175,7 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
       pairs_dw_batch_kernel<1><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_active, bv, parts);
       if (parts > 1) {
         ++t_launches;
-        pair_parts_reduce_batch_kernel<<<seg.nchunks, 256, 0, st>>>(seg, args, bv, parts);
+        if (seg_ctas(seg) > 0) pair_parts_reduce_batch_kernel<<<seg_ctas(seg), 256, 0, st>>>(seg, args, bv, parts);
       }
     }
   } else {
@@ -1196,18 +1186,22 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
 
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
                      double* h, cudaStream_t st) {
+  if (seg_ctas(t) == 0 || nvec == 0) return;
   t_launches += 2;
-  seg_dots_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, nvec, V, ldv, w, partial);
-  seg_reduce_kernel<<<dim3(t.K, nvec), 128, 0, st>>>(t, partial, h);
+  seg_dots_kernel<<<dim3(seg_ctas(t), (nvec + kSegDotVecs - 1) / kSegDotVecs), kSegThreads, 0, st>>>(t, nvec, V, ldv,
+                                                                                                     w, partial);
+  seg_reduce_kernel<<<t.K, 128, 0, st>>>(t, nvec, partial, h);
 }
 void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
                        double* w, cudaStream_t st) {
+  if (seg_ctas(t) == 0 || nvec == 0) return;
   ++t_launches;
-  seg_update_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, nvec, V, ldv, coef, sign, w);
+  seg_update_kernel<<<dim3(seg_ctas(t), kSegChunkMax / kSegUpdSub), kSegUpdSub, 0, st>>>(t, nvec, V, ldv, coef, sign, w);
 }
 void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st) {
+  if (seg_ctas(t) == 0) return;
   ++t_launches;
-  seg_scale_kernel<<<t.nchunks, kSegThreads, 0, st>>>(t, s, in, out);
+  seg_scale_kernel<<<seg_ctas(t), kSegThreads, 0, st>>>(t, s, in, out);
 }
 void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st) {
   ++t_launches;
