@@ -54,9 +54,13 @@ typedef enum {
  *  MFS_FP64   native FP64 everywhere.
  *  MFS_MIXED  GMRES passes with the operator evaluated in double-float arithmetic (pairs of
  *             FP32 values, ~2^-46 relative) on the FP32 pipes, which this GPU executes 74x
- *             faster than FP64: pair sums of steps 2+3 and the pseudo-inverse GEMVs of step 1;
- *             after each pass the residual is re-evaluated with the native FP64 operator and
- *             the correction equation solved again (iterative refinement).
+ *             faster than FP64: pair sums of steps 2+3 and the pseudo-inverse GEMVs of step 1,
+ *             where the GMRES passes read Sigma^+ U^T from its FP32 copy (half the bytes; the
+ *             operator stays accurate to ~1e-7, enough for the passes) and V in double-float;
+ *             after each pass the residual is re-evaluated with the all-double-float or the
+ *             native FP64 operator (mfs_solve_opts.residual) and the correction equation
+ *             solved again (iterative refinement).  The single-step entry points with
+ *             MFS_MIXED apply the all-double-float operator.
  *  MFS_FP32   FP32 inner GMRES on an all-FP32 operator with FP64 iterative refinement;
  *             converges only when B_k^+ amplifies by well under 1/eps_FP32, i.e. not with
  *             images and the paper's truncation 5e-12 (returns MFS_ERR_NOT_CONVERGED). */

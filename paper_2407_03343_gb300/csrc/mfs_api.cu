@@ -88,7 +88,8 @@ struct mfs_ctx {
   int state = 0;        // 0 empty, 1 spheres set, 2 built
   bool have_bc = false;
   bool solved = false;
-  bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel
+  bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel and factors
+  bool dw_fast_a = false; // with dw_pairs: Sigma^+ U^T read from its FP32 copy (inner MIXED solves)
   bool factored = false;  // one-body pseudo-inverses available
   int mode = 0;           // 0: resistance (velocities given), 1: mobility (forces/torques given)
   int n_sys = 0;          // GMRES system size: n, or n + 6P for the bordered mobility system
@@ -103,7 +104,7 @@ struct mfs_ctx {
   long long pairs_per_apply = 0, proxy_per_apply = 0, image_per_apply = 0;
   long long build_id = 0;
   struct BatchPlan* batch = nullptr;  // cached lockstep-batch workspace (owned when this is the first context)
-  double gemv_bytes32 = 0, gemv_bytes64 = 0;
+  double gemv_bytes32 = 0, gemv_bytes64 = 0, gemv_bytes_fast = 0;  // factor bytes per step 1
   int P = 0;
   double a = 1.0;
   std::vector<double> centres;
@@ -260,7 +261,8 @@ void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
     if constexpr (sizeof(T) == 8) {
       if (c->dw_pairs) {
         launch_split_dw(c->n, mu, c->d_x2, c->stream);
-        launch_gemv_dw(Ops<T>::A(c), c->d_x2, c->d_t2, nullptr, c->stream);
+        if (c->dw_fast_a) launch_gemv_f32_dw(c->gA32, c->d_x2, c->d_t2, c->stream);
+        else launch_gemv_dw(Ops<T>::A(c), c->d_x2, c->d_t2, nullptr, c->stream);
         launch_gemv_dw(Ops<T>::V(c), c->d_t2, nullptr, lam_hat, c->stream);
         return;
       }
@@ -269,7 +271,8 @@ void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
     launch_gemv<T>(Ops<T>::V(c), Ops<T>::tmp(c), lam_hat, c->stream);
   });
   c->tm.gemv_launches += 2;
-  c->tm.gemv_bytes += sizeof(T) == 8 ? c->gemv_bytes64 : c->gemv_bytes32;
+  c->tm.gemv_bytes += sizeof(T) == 8 ? (c->dw_pairs && c->dw_fast_a ? c->gemv_bytes_fast : c->gemv_bytes64)
+                                     : c->gemv_bytes32;
 }
 
 // steps 2+3 with the pair kernel of the current precision
@@ -505,6 +508,7 @@ struct BatchPlan {
   int* d_active = nullptr;
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
+  GemvBatch<float> gA32;  // the same jobs over the FP32 copies of Sigma^+ U^T (inner MIXED solves)
   SegTable seg;
   double *wb = nullptr, *x = nullptr, *r = nullptr, *e = nullptr, *w = nullptr, *lh = nullptr, *tmp = nullptr,
          *lam = nullptr, *partial = nullptr, *hbuf = nullptr, *coef = nullptr, *scl = nullptr;
@@ -606,6 +610,7 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   // GEMV jobs: every sphere of every problem, with the problems that share a context (several
   // right-hand sides on one geometry) adjacent, so a factor matrix is read once for all of them
   std::vector<const double*> mA, mV;
+  std::vector<const float*> mA32;
   std::vector<const float2*> mA2, mV2;
   std::vector<int> rA, cA, lA, rV, cV, lV, jp;
   std::vector<long long> xA, yA, xV, yV;
@@ -637,6 +642,7 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
         mA.push_back(F.A64);
         mV.push_back(F.V64);
         mA2.push_back(F.A2);
+        mA32.push_back(F.A32);
         mV2.push_back(F.V2);
         rA.push_back(F.rank); cA.push_back(F.m); lA.push_back(F.ldA);
         xA.push_back(B->voff[p] + 3LL * d.colloc_off[k]);
@@ -654,11 +660,13 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   const double** dmV = nullptr;
   const float2** dmA2 = nullptr;
   const float2** dmV2 = nullptr;
+  const float** dmA32 = nullptr;
   int *drA, *dcA, *dlA, *drV, *dcV, *dlV, *djp;
   long long *dxA, *dyA, *dxV, *dyV;
   ok = ok && put(B, dmA, mA) && put(B, dmV, mV) && put(B, drA, rA) && put(B, dcA, cA) && put(B, dlA, lA) &&
        put(B, drV, rV) && put(B, dcV, cV) && put(B, dlV, lV) && put(B, djp, jp) && put(B, dxA, xA) &&
-       put(B, dyA, yA) && put(B, dxV, xV) && put(B, dyV, yV) && put(B, dmA2, mA2) && put(B, dmV2, mV2);
+       put(B, dyA, yA) && put(B, dxV, xV) && put(B, dyV, yV) && put(B, dmA2, mA2) && put(B, dmV2, mV2) &&
+       put(B, dmA32, mA32);
   if (ok) {
     B->gA.mat_dw = dmA2;
     B->gV.mat_dw = dmV2;
@@ -666,6 +674,9 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
     B->gA.n_jobs = (int)mA.size(); B->gA.max_rows = maxA; B->gA.job_prob = djp; B->gA.active = B->d_active;
     B->gV.mat = dmV; B->gV.rows = drV; B->gV.cols = dcV; B->gV.ld = dlV; B->gV.x_off = dxV; B->gV.y_off = dyV;
     B->gV.n_jobs = (int)mV.size(); B->gV.max_rows = maxV; B->gV.job_prob = djp; B->gV.active = B->d_active;
+    B->gA32.mat = dmA32; B->gA32.rows = drA; B->gA32.cols = dcA; B->gA32.ld = dlA; B->gA32.x_off = dxA;
+    B->gA32.y_off = dyA; B->gA32.n_jobs = (int)mA32.size(); B->gA32.max_rows = maxA; B->gA32.job_prob = djp;
+    B->gA32.active = B->d_active;
   }
   // vector chunks, each inside one problem
   const long long chunk = 1024;  // enough chunks to fill the GPU for batches of small problems
@@ -734,6 +745,7 @@ struct BatchRun {
   BatchPlan* B;
   cudaStream_t st;
   bool dw;
+  bool fast_a;           // with dw: Sigma^+ U^T from its FP32 copy
   std::vector<int> act;  // host copy of the active flags
 };
 
@@ -772,7 +784,8 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
   timed(c, c->ev_gemv, [&] {
     if (R.dw) {
       launch_split_dw(B->n_total, in, B->x2, R.st);
-      launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
+      if (R.fast_a) launch_gemv_f32_dw(B->gA32, B->x2, B->t2, R.st);
+      else launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
       launch_gemv_dw(B->gV, B->t2, nullptr, B->lh, R.st);
     } else {
       launch_gemv<double>(B->gA, in, B->tmp, R.st);
@@ -809,7 +822,7 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
       c->tm.pair_image_nodes += B->image_p[p];
       c->tm.by_kind_proxy[kind] += B->proxy_p[p];
       c->tm.by_kind_image_nodes[kind] += B->image_p[p];
-      c->tm.gemv_bytes += B->key[p]->gemv_bytes64;
+      c->tm.gemv_bytes += R.dw && R.fast_a ? B->key[p]->gemv_bytes_fast : B->key[p]->gemv_bytes64;
     }
 }
 
@@ -991,7 +1004,7 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     if (s != MFS_OK) return s;
     c0->batch = B;
   }
-  BatchRun R{c0, B, c0->stream, o.precision == MFS_MIXED, std::vector<int>()};  // act empty: the first set_active uploads
+  BatchRun R{c0, B, c0->stream, o.precision == MFS_MIXED, o.precision == MFS_MIXED, std::vector<int>()};  // act empty: the first set_active uploads
   // order after the work already queued on every context's stream
   for (int p = 0; p < K; ++p)
     if (ctxs[p]->stream != R.st) {
@@ -1054,10 +1067,12 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     if ((s = set_active(R, live)) != MFS_OK) return s;
     {
       // refinement residual with the operator that dw_residual() picks (see mfs_solve)
-      const bool dw = R.dw;
+      const bool dw = R.dw, fa = R.fast_a;
       R.dw = dw_residual(o);
+      R.fast_a = false;
       batch_apply(R, B->x, B->w);
       R.dw = dw;
+      R.fast_a = fa;
     }
     launch_sub((int)n, B->wb, B->w, B->r, R.st);
     CHECK_LAUNCH(c0);
@@ -1631,15 +1646,17 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
     c->image_per_apply = ip;
     static std::atomic<long long> g_build_counter{0};
     c->build_id = ++g_build_counter;
-    double b32 = 0, b64 = 0;
+    double b32 = 0, b64 = 0, bf = 0;
     for (int k = 0; k < P && nf > 0; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
       double elems = (double)F.rank * F.m + (double)F.ncol * F.rank;
       b32 += 4.0 * elems;
       b64 += 8.0 * elems;
+      bf += 4.0 * F.rank * F.m + 8.0 * F.ncol * F.rank;
     }
     c->gemv_bytes32 = b32;
     c->gemv_bytes64 = b64;
+    c->gemv_bytes_fast = bf;
   }
   c->factored = nf > 0;
   c->solved = false;
@@ -1780,6 +1797,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
     // residual is re-evaluated with the same operator after each pass and the correction
     // equation solved again if a restart-limited pass fell short (iterative refinement).
     c->dw_pairs = (o.precision == MFS_MIXED);
+    c->dw_fast_a = c->dw_pairs;
     CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * n, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_r, c->d_wb, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     double rn = bnorm;
@@ -1792,7 +1810,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
       // solve G_hat e = r with the relative accuracy still missing, then mu += e
       if ((s = gmres<double>(c, c->d_r, c->d_w64, std::min(0.5, 0.5 * o.tol / rel), o.restart, o.max_iter - iters,
                              it_in, est)) != MFS_OK) {
-        c->dw_pairs = false;
+        c->dw_pairs = c->dw_fast_a = false;
         return s;
       }
       iters += it_in;
@@ -1805,24 +1823,26 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
       // have to contract the error, and the final accuracy is that of FP64), or, at tolerances
       // far above its accuracy floor, with the double-float operator
       c->dw_pairs = dw_residual(o);
+      c->dw_fast_a = false;
       sys_apply<double>(c, c->d_mu, c->d_w64);
       c->dw_pairs = (o.precision == MFS_MIXED);
+      c->dw_fast_a = c->dw_pairs;
       launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
       CHECK_LAUNCH(c);
       double rprev = rn;
       if ((s = norm64(c, c->d_r, rn)) != MFS_OK) {
-        c->dw_pairs = false;
+        c->dw_pairs = c->dw_fast_a = false;
         return s;
       }
       rel = rn / bnorm;
       if (it > 0) ++refinements;
       if (!std::isfinite(rn)) {
-        c->dw_pairs = false;
+        c->dw_pairs = c->dw_fast_a = false;
         return c->fail(MFS_ERR_NUMERIC, "residual is not finite");
       }
       if (rn > 0.9 * rprev && rel > o.tol) break;
     }
-    c->dw_pairs = false;
+    c->dw_pairs = c->dw_fast_a = false;
     converged = rel <= o.tol;
   } else {
     // MFS_FP32: FP64 residual, FP32 inner GMRES on the normalised residual
@@ -2029,7 +2049,7 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
     if (which == 0) apply_op<double>(c, c->d_mu, c->d_w64);
     else if (which == 1) precond<double>(c, c->d_mu, c->d_lh64);
     else pairs_step<double>(c, c->d_lam, c->d_mu, c->d_w64);
-    c->dw_pairs = false;
+    c->dw_pairs = c->dw_fast_a = false;
   } else {
     launch_convert<double, float>(len1, d1, 1.0, c->d_in32, c->stream);
     if (which == 0) {

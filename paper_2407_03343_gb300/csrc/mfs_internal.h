@@ -137,6 +137,9 @@ void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st);
 // Double-float GEMV on the FP32 pipes over b.mat_dw: x as (hi, lo) pairs; the result goes to
 // y_dw as pairs, or to y64 joined into doubles when y_dw is null.
 void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, double* y64, cudaStream_t st);
+// Double-float GEMV over an FP32 matrix (b.mat): x as (hi, lo) pairs, y_dw as pairs.  The matrix
+// rows must start 16-byte aligned (ld a multiple of 4).
+void launch_gemv_f32_dw(const GemvBatch<float>& b, const float2* x, float2* y_dw, cudaStream_t st);
 // (hi, lo) float pairs of a double vector.
 void launch_split_dw(long long n, const double* in, float2* out, cudaStream_t st);
 

@@ -824,6 +824,59 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double>
   }
 }
 
+// The same product with the matrix in FP32 (4 bytes per element): each element is an exact
+// double-word value (m, 0), so the products and sums keep double-float accuracy and only the
+// matrix itself carries FP32 rounding.  Used for Sigma^+ U^T in the inner solves of MFS_MIXED,
+// whose rounding (relative 6e-8 per element, amplified by Sigma^+ only along right singular
+// vectors whose fields on the other spheres are correspondingly weak) leaves the operator
+// accurate to ~1e-7; the refinement residual is evaluated with the double-float factors.
+__global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<float> B, const float2* __restrict__ x,
+                                                                  float2* __restrict__ y2) {
+  const int job = blockIdx.x;
+  if (B.active && !B.active[B.job_prob[job]]) return;
+  const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = (blockIdx.y * (kGemvThreads / 32) + warp) * kGemvRowsPerWarp;
+  if (r0 >= nr) return;
+  const float* M = B.mat[job];
+  const float2* xv = x + B.x_off[job];
+  dw acc[kGemvRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) acc[r] = dw{0.f, 0.f};
+  const int nq = nc / 4;  // four elements per 16-byte load
+  for (int v = lane; v < nq; v += 32) {
+    const float2 x0 = xv[4 * v], x1 = xv[4 * v + 1], x2 = xv[4 * v + 2], x3 = xv[4 * v + 3];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) {
+        float4 m = reinterpret_cast<const float4*>(M + (long long)row * ld)[v];
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.x, 0.f}, dw{x0.x, x0.y}));
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.y, 0.f}, dw{x1.x, x1.y}));
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.z, 0.f}, dw{x2.x, x2.y}));
+        acc[r] = dw_add(acc[r], dw_mul(dw{m.w, 0.f}, dw{x3.x, x3.y}));
+      }
+    }
+  }
+  for (int cidx = 4 * nq + lane; cidx < nc; cidx += 32) {
+    const float2 xa = xv[cidx];
+#pragma unroll
+    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+      int row = r0 + r;
+      if (row < nr) acc[r] = dw_add(acc[r], dw_mul(dw{M[(long long)row * ld + cidx], 0.f}, dw{xa.x, xa.y}));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+    dw s = acc[r];
+    for (int o = 16; o > 0; o >>= 1) {
+      dw t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
+      s = dw_add(s, t);
+    }
+    if (lane == 0 && r0 + r < nr) y2[B.y_off[job] + r0 + r] = make_float2(s.h, s.l);
+  }
+}
+
 __global__ void split_dw_kernel(long long n, const double* __restrict__ in, float2* __restrict__ out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     dw s = dw_split(in[e]);
@@ -1225,6 +1278,14 @@ void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, d
   ++t_launches;
   if (y_dw) gemv_dw_kernel<false><<<grid, kGemvThreads, 0, st>>>(b, x, y_dw, nullptr);
   else gemv_dw_kernel<true><<<grid, kGemvThreads, 0, st>>>(b, x, nullptr, y64);
+}
+
+void launch_gemv_f32_dw(const GemvBatch<float>& b, const float2* x, float2* y_dw, cudaStream_t st) {
+  if (b.n_jobs == 0 || b.max_rows == 0) return;
+  const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
+  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
+  ++t_launches;
+  gemv_f32dw_kernel<<<grid, kGemvThreads, 0, st>>>(b, x, y_dw);
 }
 
 void launch_split_dw(long long n, const double* in, float2* out, cudaStream_t st) {
