@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 sweep and FP32 kernel side runs")
+    ap.add_argument("--restart", type=int, default=300, help="GMRES restart length of the timed solves")
     ap.add_argument("--kernel-case", type=int, default=0,
                     help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
     return ap.parse_args()
@@ -61,7 +62,7 @@ def workload_config(args):
     from paper_2407_03343_gb300 import workloads
     return {"workload": "gap sweep: 2 unit spheres x 18 gaps in [1e-3, 1] x 3 motions (54 resistance solves)",
             "n_proxy": N_PROXY, "r_proxy": R_PROXY, "m_basic": M_BASIC, "n_im": "rule, <= 20",
-            "eps_trunc": 5e-12, "gmres_tol": 1e-6, "precision": args.precision,
+            "eps_trunc": 5e-12, "gmres_tol": 1e-6, "gmres_restart": args.restart, "precision": args.precision,
             "gaps": [float(g) for g in workloads.gap_sweep_gaps()],
             "l2": "256 MB write between timed steps; resident factors ~5 GB exceed L2"}
 
@@ -250,7 +251,7 @@ def main():
     sizes = [c.sizes() for c in ctxs]
 
     prec = args.precision
-    opts = mfs.default_solve_opts(precision=prec, tol=1e-6)
+    opts = mfs.default_solve_opts(precision=prec, tol=1e-6, restart=args.restart)
     if args.kernel_case:
         v, w = workloads.motion("squeeze")
         for c in ctxs:
