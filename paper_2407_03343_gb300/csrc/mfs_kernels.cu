@@ -824,9 +824,12 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double>
   }
 }
 
-// The same product with the matrix in FP32 (4 bytes per element): each element is an exact
-// double-word value (m, 0), so the products and sums keep double-float accuracy and only the
-// matrix itself carries FP32 rounding.  Used for Sigma^+ U^T in the inner solves of MFS_MIXED,
+// The same product with the matrix in FP32 (4 bytes per element).  Per element the product
+// m (x_hi + x_lo) is formed exactly up to the rounding of its small part (TwoProd), the running
+// FP32 sum's rounding error is captured by TwoSum, and the error terms are summed in a second
+// float that is folded in once per lane: ~11 instructions per element instead of a full
+// double-word product and sum, with an accumulation error (~n^2 eps^2 for n terms per lane)
+// far below the FP32 rounding of the matrix itself, which is the only real error.  Used for Sigma^+ U^T in the inner solves of MFS_MIXED,
 // whose rounding (relative 6e-8 per element, amplified by Sigma^+ only along right singular
 // vectors whose fields on the other spheres are correspondingly weak) leaves the operator
 // accurate to ~1e-7; the refinement residual is evaluated with the double-float factors.
@@ -840,9 +843,16 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<floa
   if (r0 >= nr) return;
   const float* M = B.mat[job];
   const float2* xv = x + B.x_off[job];
-  dw acc[kGemvRowsPerWarp];
+  float sh[kGemvRowsPerWarp], sl[kGemvRowsPerWarp];
 #pragma unroll
-  for (int r = 0; r < kGemvRowsPerWarp; ++r) acc[r] = dw{0.f, 0.f};
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) sh[r] = sl[r] = 0.f;
+  auto add = [](float& h, float& l, float m, float2 xe) {
+    dw p = two_prod(m, xe.x);
+    p.l = __fmaf_rn(m, xe.y, p.l);
+    dw t = two_sum(h, p.h);
+    h = t.h;
+    l = __fadd_rn(l, __fadd_rn(t.l, p.l));
+  };
   const int nq = nc / 4;  // four elements per 16-byte load
   for (int v = lane; v < nq; v += 32) {
     const float2 x0 = xv[4 * v], x1 = xv[4 * v + 1], x2 = xv[4 * v + 2], x3 = xv[4 * v + 3];
@@ -851,10 +861,10 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<floa
       int row = r0 + r;
       if (row < nr) {
         float4 m = reinterpret_cast<const float4*>(M + (long long)row * ld)[v];
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.x, 0.f}, dw{x0.x, x0.y}));
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.y, 0.f}, dw{x1.x, x1.y}));
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.z, 0.f}, dw{x2.x, x2.y}));
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.w, 0.f}, dw{x3.x, x3.y}));
+        add(sh[r], sl[r], m.x, x0);
+        add(sh[r], sl[r], m.y, x1);
+        add(sh[r], sl[r], m.z, x2);
+        add(sh[r], sl[r], m.w, x3);
       }
     }
   }
@@ -863,12 +873,12 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<floa
 #pragma unroll
     for (int r = 0; r < kGemvRowsPerWarp; ++r) {
       int row = r0 + r;
-      if (row < nr) acc[r] = dw_add(acc[r], dw_mul(dw{M[(long long)row * ld + cidx], 0.f}, dw{xa.x, xa.y}));
+      if (row < nr) add(sh[r], sl[r], M[(long long)row * ld + cidx], xa);
     }
   }
 #pragma unroll
   for (int r = 0; r < kGemvRowsPerWarp; ++r) {
-    dw s = acc[r];
+    dw s = two_sum(sh[r], sl[r]);
     for (int o = 16; o > 0; o >>= 1) {
       dw t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
       s = dw_add(s, t);
