@@ -713,6 +713,7 @@ __global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double
 // ------------------------------------------------------------------ batched GEMV
 constexpr int kGemvThreads = 256;
 constexpr int kGemvRowsPerWarp = 2;
+constexpr int kGemvDepth = 4;  // 16-byte loads per row and lane in flight in the double-float GEMVs
 
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int w = 4; };
@@ -786,16 +787,27 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double>
 #pragma unroll
   for (int r = 0; r < kGemvRowsPerWarp; ++r) acc[r] = dw{0.f, 0.f};
   const int npair = nc / 2;  // two elements per 16-byte load
-  for (int v = lane; v < npair; v += 32) {
-    const float2 xa = xv[2 * v], xb = xv[2 * v + 1];
+  // kGemvDepth loads per row and lane issued before they are used, so that enough bytes are
+  // in flight even when few jobs are active (the lockstep tail)
+  for (int v0 = lane; v0 < npair; v0 += 32 * kGemvDepth) {
+    float4 m[kGemvDepth][kGemvRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
-      int row = r0 + r;
-      if (row < nr) {
-        float4 m = reinterpret_cast<const float4*>(M + (long long)row * ld)[v];
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.x, m.y}, dw{xa.x, xa.y}));
-        acc[r] = dw_add(acc[r], dw_mul(dw{m.z, m.w}, dw{xb.x, xb.y}));
-      }
+    for (int u = 0; u < kGemvDepth; ++u)
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r)
+        if (v0 + 32 * u < npair && r0 + r < nr)
+          m[u][r] = reinterpret_cast<const float4*>(M + (long long)(r0 + r) * ld)[v0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kGemvDepth; ++u) {
+      const int v = v0 + 32 * u;
+      if (v >= npair) break;
+      const float2 xa = xv[2 * v], xb = xv[2 * v + 1];
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r)
+        if (r0 + r < nr) {
+          acc[r] = dw_add(acc[r], dw_mul(dw{m[u][r].x, m[u][r].y}, dw{xa.x, xa.y}));
+          acc[r] = dw_add(acc[r], dw_mul(dw{m[u][r].z, m[u][r].w}, dw{xb.x, xb.y}));
+        }
     }
   }
   for (int cidx = 2 * npair + lane; cidx < nc; cidx += 32) {
@@ -854,18 +866,27 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<floa
     l = __fadd_rn(l, __fadd_rn(t.l, p.l));
   };
   const int nq = nc / 4;  // four elements per 16-byte load
-  for (int v = lane; v < nq; v += 32) {
-    const float2 x0 = xv[4 * v], x1 = xv[4 * v + 1], x2 = xv[4 * v + 2], x3 = xv[4 * v + 3];
+  for (int v0 = lane; v0 < nq; v0 += 32 * kGemvDepth) {
+    float4 m[kGemvDepth][kGemvRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kGemvRowsPerWarp; ++r) {
-      int row = r0 + r;
-      if (row < nr) {
-        float4 m = reinterpret_cast<const float4*>(M + (long long)row * ld)[v];
-        add(sh[r], sl[r], m.x, x0);
-        add(sh[r], sl[r], m.y, x1);
-        add(sh[r], sl[r], m.z, x2);
-        add(sh[r], sl[r], m.w, x3);
-      }
+    for (int u = 0; u < kGemvDepth; ++u)
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r)
+        if (v0 + 32 * u < nq && r0 + r < nr)
+          m[u][r] = reinterpret_cast<const float4*>(M + (long long)(r0 + r) * ld)[v0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < kGemvDepth; ++u) {
+      const int v = v0 + 32 * u;
+      if (v >= nq) break;
+      const float2 x0 = xv[4 * v], x1 = xv[4 * v + 1], x2 = xv[4 * v + 2], x3 = xv[4 * v + 3];
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r)
+        if (r0 + r < nr) {
+          add(sh[r], sl[r], m[u][r].x, x0);
+          add(sh[r], sl[r], m[u][r].y, x1);
+          add(sh[r], sl[r], m[u][r].z, x2);
+          add(sh[r], sl[r], m[u][r].w, x3);
+        }
     }
   }
   for (int cidx = 4 * nq + lane; cidx < nc; cidx += 32) {
