@@ -113,6 +113,36 @@ def suspension(P: int, phi: float, seed: int, radius: float = 1.0, gap_lo: float
     return centres
 
 
+def tetrahedron(delta: float, radius: float = 1.0):
+    """Four spheres on the vertices of a regular tetrahedron, every pair delta (radius units) apart."""
+    a = radius
+    edge = (2.0 + delta) * a
+    v = np.array([[1.0, 1.0, 1.0], [1.0, -1.0, -1.0], [-1.0, 1.0, -1.0], [-1.0, -1.0, 1.0]])
+    return v * (edge / (2.0 * math.sqrt(2.0)))
+
+
+def cluster(P: int, gap: float, seed: int, radius: float = 1.0, max_tries: int = 100000):
+    """P spheres grown one at a time, each placed `gap` from a randomly chosen earlier sphere in
+    a random direction and at least `gap` from all others, so that every sphere has a neighbour
+    exactly `gap` away."""
+    rng = np.random.default_rng(seed)
+    a = radius
+    centres = np.zeros((P, 3))
+    n, tries = 1, 0
+    while n < P:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not grow the cluster")
+        i = int(rng.integers(0, n))
+        c = centres[i] + (2.0 + gap) * a * _random_unit(rng)
+        d = np.linalg.norm(centres[:n] - c[None, :], axis=1)
+        d[i] = np.inf
+        if np.all(d >= (2.0 + gap) * a * (1.0 - 1e-12)):
+            centres[n] = c
+            n += 1
+    return centres
+
+
 def rigid_velocities(P: int, seed: int):
     rng = np.random.default_rng(seed)
     return rng.normal(size=(P, 3)), rng.normal(size=(P, 3))
