@@ -488,6 +488,7 @@ struct BatchPlan {
   std::vector<long long> voff, uoff, toff;
   std::vector<long long> pairs_p, proxy_p, image_p;
   std::vector<void*> allocs;
+  std::vector<void*> gs_allocs;
   void* d_args = nullptr;    // per-problem kernel arguments for 4 nodes per thread
   void* d_args1 = nullptr;   // and for 1 node per thread
   int2* d_work = nullptr;    // (problem, tile) lists for both tilings
@@ -505,6 +506,9 @@ struct BatchPlan {
   std::vector<int> cprob_host;  // problem of each vector chunk
   int* d_cchunk = nullptr;      // compacted chunk list of the active problems (seg.list)
   int* cpin = nullptr;          // pinned staging for it
+  GivensState gs;               // device GMRES state (restart_cap columns per problem)
+  int gs_restart = 0;
+  int* snap = nullptr;          // pinned: kSyncEvery x K active-flag snapshots, then the error flag
   int* d_active = nullptr;
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
@@ -527,6 +531,8 @@ struct BatchPlan {
     if (apin) cudaFreeHost(apin);
     if (wpin) cudaFreeHost(wpin);
     if (cpin) cudaFreeHost(cpin);
+    if (snap) cudaFreeHost(snap);
+    for (void* q : gs_allocs) cudaFree(q);
     if (ev) cudaEventDestroy(ev);
   }
   template <typename T>
@@ -777,8 +783,8 @@ mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
   return MFS_OK;
 }
 
-// out = G_hat in for every active problem
-void batch_apply(BatchRun& R, const double* in, double* out) {
+// out = G_hat in for every problem the device flags mark active (the host's R.act picks the tiling)
+void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
   mfs_ctx* c = R.c0;
   BatchPlan* B = R.B;
   timed(c, c->ev_gemv, [&] {
@@ -815,8 +821,15 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
   const int kind = c->tm.pair_kind;
   c->tm.by_kind_launches[kind] += 1;
   if (c->prof) c->ev_pair_kind.push_back(kind);
+}
+
+// work counters of one batched apply over the problems of `act`
+void batch_apply_count(BatchRun& R, const std::vector<int>& act) {
+  mfs_ctx* c = R.c0;
+  BatchPlan* B = R.B;
+  const int kind = R.dw ? MFS_MIXED : MFS_FP64;
   for (int p = 0; p < B->K; ++p)
-    if (R.act[p]) {
+    if (act[p]) {
       c->tm.pair_interactions += B->pairs_p[p];
       c->tm.pair_proxy += B->proxy_p[p];
       c->tm.pair_image_nodes += B->image_p[p];
@@ -824,6 +837,11 @@ void batch_apply(BatchRun& R, const double* in, double* out) {
       c->tm.by_kind_image_nodes[kind] += B->image_p[p];
       c->tm.gemv_bytes += R.dw && R.fast_a ? B->key[p]->gemv_bytes_fast : B->key[p]->gemv_bytes64;
     }
+}
+
+void batch_apply(BatchRun& R, const double* in, double* out) {
+  batch_apply_kernels(R, in, out);
+  batch_apply_count(R, R.act);
 }
 
 // per-problem 2-norms of v (active problems; others 0)
@@ -838,7 +856,56 @@ mfs_status batch_norms(BatchRun& R, const double* v, std::vector<double>& nrm) {
   return MFS_OK;
 }
 
+constexpr int kSyncEvery = 4;  // lockstep GMRES steps between host synchronisations
+
+// Device GMRES state for `restart` steps (kept across calls, grown when needed).
+mfs_status ensure_givens(BatchRun& R, int restart) {
+  BatchPlan* B = R.B;
+  if (B->gs_restart >= restart && B->snap) return MFS_OK;
+  for (void* q : B->gs_allocs) cudaFree(q);
+  B->gs_allocs.clear();
+  B->gs_restart = 0;
+  const int K = B->K, ldh = restart + 1;
+  auto get = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    B->gs_allocs.push_back(q);
+    return q;
+  };
+  GivensState& S = B->gs;
+  S.K = K;
+  S.ldh = ldh;
+  S.restart = restart;
+  S.H = (double*)get(sizeof(double) * (size_t)K * restart * ldh);
+  S.cs = (double*)get(sizeof(double) * (size_t)K * restart);
+  S.sn = (double*)get(sizeof(double) * (size_t)K * restart);
+  S.g = (double*)get(sizeof(double) * (size_t)K * ldh);
+  S.bn = (double*)get(sizeof(double) * K);
+  S.tol = (double*)get(sizeof(double) * K);
+  S.est = (double*)get(sizeof(double) * K);
+  S.iters = (int*)get(sizeof(int) * K);
+  S.jused = (int*)get(sizeof(int) * K);
+  S.err = (int*)get(sizeof(int));
+  S.active = B->d_active;
+  S.scl = B->scl;
+  if (!S.H || !S.cs || !S.sn || !S.g || !S.bn || !S.tol || !S.est || !S.iters || !S.jused || !S.err)
+    return R.c0->fail(MFS_ERR_OOM, "device allocation failed: batched GMRES state");
+  // snapshots, then one slot for the error flag
+  if (!B->snap && cudaMallocHost(&B->snap, sizeof(int) * ((size_t)kSyncEvery * K + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return R.c0->fail(MFS_ERR_OOM, "pinned allocation failed: batched GMRES flags");
+  }
+  B->gs_restart = restart;
+  return MFS_OK;
+}
+
 // One GMRES cycle (at most `restart` iterations) from x = 0 for the problems with solve[p] = 1.
+// The Hessenberg updates, the convergence tests and the retirement of converged problems run on
+// the device; the host synchronises every kSyncEvery steps to refresh its view of the active
+// set (compacted launch lists, work counters) and to stop once every problem has converged.
 mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std::vector<int>& solve,
                              const std::vector<double>& tol, int restart, int iter_budget, std::vector<int>& iters,
                              std::vector<double>& est) {
@@ -859,6 +926,10 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
     }
     B->basis_cap = need;
   }
+  if ((s = ensure_givens(R, restart)) != MFS_OK) return s;
+  GivensState S = B->gs;
+  S.ldh = ldh;
+  S.restart = restart;
   double* V = B->basis;
   CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * n, R.st));
   if ((s = set_active(R, solve)) != MFS_OK) return s;
@@ -872,91 +943,90 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
     }
   if ((s = set_active(R, act)) != MFS_OK) return s;
   const std::vector<int> started(act);
-  std::vector<double> sc(K, 0.0);
-  for (int p = 0; p < K; ++p) sc[p] = act[p] ? 1.0 / bn[p] : 0.0;
-  CUDA_TRY(c, cudaMemcpyAsync(B->scl, sc.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
-  launch_seg_scale(B->seg, B->scl, b, V, R.st);
-  std::vector<std::vector<double>> H(K), cs(K), sn(K), g(K);
-  std::vector<int> jused(K, 0);
+  // initial state: V_0 = b / ||b||, g = (||b||, 0, ...)
+  std::vector<double> sc(K, 0.0), g0((size_t)K * ldh, 0.0), bnd(K, 1.0);
   for (int p = 0; p < K; ++p)
     if (act[p]) {
-      H[p].assign((size_t)ldh * restart, 0.0);
-      cs[p].assign(restart, 0.0);
-      sn[p].assign(restart, 0.0);
-      g[p].assign(ldh, 0.0);
-      g[p][0] = bn[p];
+      sc[p] = 1.0 / bn[p];
+      g0[(size_t)p * ldh] = bn[p];
+      bnd[p] = bn[p];
       est[p] = 1.0;
     }
+  CUDA_TRY(c, cudaMemcpyAsync(B->scl, sc.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+  CUDA_TRY(c, cudaMemcpyAsync(S.g, g0.data(), sizeof(double) * g0.size(), cudaMemcpyHostToDevice, R.st));
+  CUDA_TRY(c, cudaMemcpyAsync(const_cast<double*>(S.bn), bnd.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+  CUDA_TRY(c, cudaMemcpyAsync(const_cast<double*>(S.tol), tol.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+  CUDA_TRY(c, cudaMemsetAsync(S.iters, 0, sizeof(int) * K, R.st));
+  CUDA_TRY(c, cudaMemsetAsync(S.jused, 0, sizeof(int) * K, R.st));
+  CUDA_TRY(c, cudaMemsetAsync(S.err, 0, sizeof(int), R.st));
+  launch_seg_scale(B->seg, B->scl, b, V, R.st);
   double* h1 = B->hbuf;
   double* h2 = B->hbuf + (size_t)kMaxBatchVec * K;
   double* hn = B->hbuf + (size_t)2 * kMaxBatchVec * K;
-  int used = 0;
-  for (int j = 0; j < restart && used < iter_budget; ++j) {
-    bool any = false;
-    for (int p = 0; p < K; ++p) any = any || act[p];
-    if (!any) break;
+  // the steps since the last synchronisation: flags after each step, for the work counters
+  std::vector<int> window_start(act);
+  int in_window = 0, used = 0;
+  bool any = true;
+  for (int j = 0; j < restart && used < iter_budget && any; ++j) {
     double* w = V + (size_t)(j + 1) * n;
-    batch_apply(R, V + (size_t)j * n, w);
+    batch_apply_kernels(R, V + (size_t)j * n, w);
     launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h1, R.st);
     launch_seg_update(B->seg, j + 1, V, n, h1, -1.0, w, R.st);
     launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h2, R.st);
     launch_seg_update(B->seg, j + 1, V, n, h2, -1.0, w, R.st);
     launch_seg_dots(B->seg, 1, w, n, w, B->partial, hn, R.st);
-    CHECK_LAUNCH(c);
-    double* hp = B->hpin;
-    CUDA_TRY(c, cudaMemcpyAsync(hp, h1, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, R.st));
-    CUDA_TRY(c, cudaMemcpyAsync(hp + (size_t)kMaxBatchVec * K, h2, sizeof(double) * (j + 1) * K, cudaMemcpyDeviceToHost, R.st));
-    CUDA_TRY(c, cudaMemcpyAsync(hp + (size_t)2 * kMaxBatchVec * K, hn, sizeof(double) * K, cudaMemcpyDeviceToHost, R.st));
-    CUDA_TRY(c, cudaStreamSynchronize(R.st));
-    ++used;
-    std::vector<int> next(act);
-    for (int p = 0; p < K; ++p) {
-      if (!act[p]) continue;
-      double* col = &H[p][(size_t)j * ldh];
-      for (int i = 0; i <= j; ++i) col[i] = hp[(size_t)i * K + p] + hp[(size_t)kMaxBatchVec * K + (size_t)i * K + p];
-      const double hnext = std::sqrt(std::max(0.0, hp[(size_t)2 * kMaxBatchVec * K + p]));
-      if (!std::isfinite(hnext)) return c->fail(MFS_ERR_NUMERIC, "non-finite value in the batched Arnoldi process");
-      col[j + 1] = hnext;
-      for (int i = 0; i < j; ++i) {
-        double t = cs[p][i] * col[i] + sn[p][i] * col[i + 1];
-        col[i + 1] = -sn[p][i] * col[i] + cs[p][i] * col[i + 1];
-        col[i] = t;
-      }
-      const double den = std::hypot(col[j], col[j + 1]);
-      cs[p][j] = den > 0 ? col[j] / den : 1.0;
-      sn[p][j] = den > 0 ? col[j + 1] / den : 0.0;
-      col[j] = den;
-      col[j + 1] = 0.0;
-      g[p][j + 1] = -sn[p][j] * g[p][j];
-      g[p][j] = cs[p][j] * g[p][j];
-      jused[p] = j + 1;
-      ++iters[p];
-      est[p] = std::fabs(g[p][j + 1]) / bn[p];
-      sc[p] = hnext > 0 ? 1.0 / hnext : 0.0;
-      if (est[p] <= tol[p] || hnext == 0.0) next[p] = 0;
-    }
-    CUDA_TRY(c, cudaMemcpyAsync(B->scl, sc.data(), sizeof(double) * K, cudaMemcpyHostToDevice, R.st));
+    launch_batch_givens(S, j, h1, h2, hn, R.st);
     launch_seg_scale(B->seg, B->scl, w, w, R.st);
-    act = next;
-    if ((s = set_active(R, act)) != MFS_OK) return s;
-  }
-  // x = V y per problem, y = R^{-1} g (zero beyond the problem's own iterations)
-  int jmax = 0;
-  for (int p = 0; p < K; ++p) jmax = std::max(jmax, jused[p]);
-  if (jmax == 0) return MFS_OK;
-  std::vector<double> cf((size_t)jmax * K, 0.0);
-  for (int p = 0; p < K; ++p) {
-    const int J = jused[p];
-    std::vector<double> y(J, 0.0);
-    for (int i = J - 1; i >= 0; --i) {
-      double t = g[p][i];
-      for (int q = i + 1; q < J; ++q) t -= H[p][(size_t)q * ldh + i] * y[q];
-      const double diag = H[p][(size_t)i * ldh + i];
-      y[i] = diag != 0.0 ? t / diag : 0.0;
+    CHECK_LAUNCH(c);
+    CUDA_TRY(c, cudaMemcpyAsync(B->snap + (size_t)in_window * K, B->d_active, sizeof(int) * K, cudaMemcpyDeviceToHost,
+                                R.st));
+    ++in_window;
+    ++used;
+    if (in_window == kSyncEvery || j + 1 == restart || used >= iter_budget) {
+      int* herr = B->snap + (size_t)kSyncEvery * K;
+      CUDA_TRY(c, cudaMemcpyAsync(herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, R.st));
+      CUDA_TRY(c, cudaStreamSynchronize(R.st));
+      if (*herr) return c->fail(MFS_ERR_NUMERIC, "non-finite value in the batched Arnoldi process");
+      // the apply of each step ran over the flags left by the step before it
+      std::vector<int> cur(window_start);
+      for (int t = 0; t < in_window; ++t) {
+        batch_apply_count(R, cur);
+        cur.assign(B->snap + (size_t)t * K, B->snap + (size_t)(t + 1) * K);
+      }
+      in_window = 0;
+      window_start = cur;
+      any = false;
+      for (int p = 0; p < K; ++p) any = any || cur[p];
+      if (any && (s = set_active(R, cur)) != MFS_OK) return s;
     }
-    for (int i = 0; i < J; ++i) cf[(size_t)i * K + p] = y[i];
   }
-  CUDA_TRY(c, cudaMemcpyAsync(B->coef, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, R.st));
+  // the device flags were changed by the Givens kernel: the next set_active must upload
+  R.act.clear();
+  if (in_window > 0) {
+    // left the loop between synchronisations (every problem converged): count the last steps
+    CUDA_TRY(c, cudaStreamSynchronize(R.st));
+    std::vector<int> cur(window_start);
+    for (int t = 0; t < in_window; ++t) {
+      batch_apply_count(R, cur);
+      cur.assign(B->snap + (size_t)t * K, B->snap + (size_t)(t + 1) * K);
+    }
+  }
+  // per-problem counts and estimates, then x = V y with y = R^{-1} g
+  std::vector<int> it_dev(K), jused(K);
+  std::vector<double> est_dev(K);
+  CUDA_TRY(c, cudaMemcpyAsync(it_dev.data(), S.iters, sizeof(int) * K, cudaMemcpyDeviceToHost, R.st));
+  CUDA_TRY(c, cudaMemcpyAsync(jused.data(), S.jused, sizeof(int) * K, cudaMemcpyDeviceToHost, R.st));
+  CUDA_TRY(c, cudaMemcpyAsync(est_dev.data(), S.est, sizeof(double) * K, cudaMemcpyDeviceToHost, R.st));
+  CUDA_TRY(c, cudaStreamSynchronize(R.st));
+  int jmax = 0;
+  for (int p = 0; p < K; ++p) {
+    if (!started[p]) continue;
+    iters[p] += it_dev[p];
+    if (jused[p] > 0) est[p] = est_dev[p];
+    jmax = std::max(jmax, jused[p]);
+  }
+  if (jmax == 0) return MFS_OK;
+  launch_batch_backsolve(S, jmax, B->coef, R.st);
   if ((s = set_active(R, started)) != MFS_OK) return s;
   launch_seg_update(B->seg, jmax, V, n, B->coef, 1.0, x, R.st);
   CHECK_LAUNCH(c);

@@ -184,6 +184,34 @@ void launch_seg_update(const SegTable& t, int nvec, const double* V, long long l
 void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st);
 void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st);
 
+// Device-resident GMRES state of a lockstep batch of K problems: per problem `restart`
+// Hessenberg columns of ldh = restart + 1 entries, the Givens rotations, the rotated right-hand
+// side g (g_0 = ||b||), its norm bn, the tolerance, the residual estimate, the step counts, the
+// active flags (shared with the batch kernels), the scale of the next basis vector and an error
+// flag (a non-finite Arnoldi value).
+constexpr int kMaxGmresCol = 512;  // restart + 1 must not exceed this (the batch limit)
+struct GivensState {
+  double* H = nullptr;
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* g = nullptr;
+  const double* bn = nullptr;
+  const double* tol = nullptr;
+  double* est = nullptr;
+  int* iters = nullptr;
+  int* jused = nullptr;
+  int* active = nullptr;
+  double* scl = nullptr;
+  int* err = nullptr;
+  int K = 0, ldh = 0, restart = 0;
+};
+// Arnoldi step j from the CGS2 dot products h1, h2 (vector-major, h[i K + p]) and the squared
+// norm hn of the orthogonalised vector; deactivates converged problems.
+void launch_batch_givens(const GivensState& S, int j, const double* h1, const double* h2, const double* hn,
+                         cudaStream_t st);
+// coef[i K + p] = (R^{-1} g)_i over each problem's jused steps, zero up to jmax.
+void launch_batch_backsolve(const GivensState& S, int jmax, double* coef, cudaStream_t st);
+
 // Forces and torques (Sec. 2.3 remark), FP64, one CTA per sphere.
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st);
 // the same with F, T written every `stride` doubles per sphere and scaled by sF, sT

@@ -1069,6 +1069,87 @@ __global__ void axpy64_kernel(long long n, double a, const double* __restrict__ 
     y[e] += a * x[e];
 }
 
+// ------------------------------------------------------------------ batched Givens (device)
+// One Arnoldi step for every active problem of a lockstep batch, one thread per problem: the
+// Hessenberg column h = h1 + h2 (the two classical Gram-Schmidt passes) with the subdiagonal
+// sqrt(hn), the earlier Givens rotations applied, a new rotation formed, the least-squares
+// right-hand side g rotated and the residual estimate |g_{j+1}| / ||b|| updated.  A problem that
+// meets its tolerance (or breaks down) is deactivated here, on the device, so the host need
+// not wait for every step; scl = 1 / h_{j+1,j} normalises the new basis vector.
+// One CTA per problem: the column and the rotations are staged in shared memory in parallel,
+// one thread runs the sequential rotation chain there, and the column is written back.
+__global__ void batch_givens_kernel(GivensState S, int j, const double* __restrict__ h1, const double* __restrict__ h2,
+                                    const double* __restrict__ hn) {
+  const int p = blockIdx.x;
+  if (!S.active[p]) return;
+  __shared__ double col[kMaxGmresCol + 1], cs[kMaxGmresCol], sn[kMaxGmresCol];
+  __shared__ int done;
+  double* colg = S.H + ((long long)p * S.restart + j) * S.ldh;
+  double* csg = S.cs + (long long)p * S.restart;
+  double* sng = S.sn + (long long)p * S.restart;
+  double* g = S.g + (long long)p * S.ldh;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = h1[(long long)i * S.K + p] + h2[(long long)i * S.K + p];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs[i] = csg[i];
+    sn[i] = sng[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    done = 0;
+    const double hnext = sqrt(fmax(0.0, hn[p]));
+    if (!isfinite(hnext)) {
+      S.err[0] = 1;
+      S.active[p] = 0;
+      done = 1;
+    } else {
+      col[j + 1] = hnext;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      const double den = hypot(col[j], col[j + 1]);
+      const double c = den > 0 ? col[j] / den : 1.0, sj = den > 0 ? col[j + 1] / den : 0.0;
+      csg[j] = c;
+      sng[j] = sj;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sj * g[j];
+      g[j] = c * g[j];
+      S.jused[p] = j + 1;
+      S.iters[p] += 1;
+      S.est[p] = fabs(g[j + 1]) / S.bn[p];
+      S.scl[p] = hnext > 0 ? 1.0 / hnext : 0.0;
+      if (S.est[p] <= S.tol[p] || hnext == 0.0) S.active[p] = 0;
+    }
+  }
+  __syncthreads();
+  if (done) return;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) colg[i] = col[i];
+}
+
+// y = R^{-1} g per problem (back substitution over its own jused steps): coef[i K + p] = y_i,
+// zero for jused <= i < jmax
+__global__ void batch_backsolve_kernel(GivensState S, int jmax, double* __restrict__ coef) {
+  const int p = blockIdx.x;
+  const int J = S.jused[p];
+  const double* H = S.H + (long long)p * S.restart * S.ldh;
+  const double* g = S.g + (long long)p * S.ldh;
+  __shared__ double t[kMaxGmresCol];
+  // column-oriented back substitution: after y_i is known, every thread updates t[q] -= R[q][i] y_i
+  for (int q = threadIdx.x; q < J; q += blockDim.x) t[q] = g[q];
+  __syncthreads();
+  for (int i = J - 1; i >= 0; --i) {
+    const double d = H[(long long)i * S.ldh + i];
+    const double yi = d != 0.0 ? t[i] / d : 0.0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < i; q += blockDim.x) t[q] -= H[(long long)i * S.ldh + q] * yi;
+    if (threadIdx.x == 0) coef[(long long)i * S.K + p] = yi;
+    __syncthreads();
+  }
+  for (int i = J + threadIdx.x; i < jmax; i += blockDim.x) coef[(long long)i * S.K + p] = 0.0;
+}
+
 // ------------------------------------------------------------------ forces / torques
 __global__ void ft_kernel(int N, const double* __restrict__ proxy64, const double* __restrict__ img64,
                           const int* __restrict__ img_off, const long long* __restrict__ unk_off,
@@ -1286,6 +1367,15 @@ void launch_seg_scale(const SegTable& t, const double* s, const double* in, doub
   if (seg_ctas(t) == 0) return;
   ++t_launches;
   seg_scale_kernel<<<seg_ctas(t), kSegThreads, 0, st>>>(t, s, in, out);
+}
+void launch_batch_givens(const GivensState& S, int j, const double* h1, const double* h2, const double* hn,
+                         cudaStream_t st) {
+  ++t_launches;
+  batch_givens_kernel<<<S.K, 128, 0, st>>>(S, j, h1, h2, hn);
+}
+void launch_batch_backsolve(const GivensState& S, int jmax, double* coef, cudaStream_t st) {
+  ++t_launches;
+  batch_backsolve_kernel<<<S.K, 128, 0, st>>>(S, jmax, coef);
 }
 void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st) {
   ++t_launches;
