@@ -38,6 +38,10 @@ MOTIONS = ("squeeze", "shear", "rotate")
 # (204 instructions, 44 of them FMAs) per Stokeslet pair and 544 (436, 108 FMAs) per image
 # triple, counted from the kernel source.
 FLOPS = {"fp32": (28.0, 63.0), "mixed": (248.0, 544.0)}
+# dram__bytes_read.sum + dram__bytes_write.sum of one pairs_dw_batch_kernel<1> launch over the 18
+# gap-sweep problems (ncu --set full on `bench.py --kernel-case 20`; 5.05 MB read, 0 written):
+# the kernel is FP32-issue-bound and its operands stay in L2
+PAIR_DW_TRAFFIC_BYTES = 5.055e6
 
 
 def parse():
@@ -357,7 +361,10 @@ def main():
     roofline = {"bound": "alu", "kernel": "pairs_dw_kernel" if prec == "mixed" else "pairs_kernel<double>",
                 "achieved": achieved_tflops, "peak": fp32_peak if prec == "mixed" else 1.0,
                 "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak if prec == "mixed" else 1.0),
-                "traffic": None,
+                # dram read + write of one captured launch (ncu, 18 gap-sweep problems, see profiles/)
+                "traffic": PAIR_DW_TRAFFIC_BYTES if prec == "mixed" else None,
+                "traffic_launch": "pairs_dw_batch_kernel<1>, 18-problem launch of --kernel-case 20"
+                if prec == "mixed" else None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock under load"
                 if prec == "mixed" else "FP64 DFMA measured 1.0 TFLOP/s",
                 "avg_launch_us": 1000.0 * k_ms / max(k_launch, 1),

@@ -695,19 +695,19 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const Pair
   A.out = bv.out + bv.voff[w.x];
   pair_tile_dw<NT>(A, w.y, blockIdx.x % nparts, nparts, bv.partial + bv.voff[w.x], bv.pstride);
 }
-// the batched counterpart of pair_parts_reduce_kernel, one CTA per vector chunk of an active problem
+// the batched counterpart of pair_parts_reduce_kernel: CTA (chunk of an active problem, piece of
+// blockDim elements), so that a single short problem still gets enough CTAs
 __global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double>* __restrict__ args, BatchVecs bv,
                                                int nparts) {
   const int b = t.list ? t.list[blockIdx.x] : blockIdx.x;
   const int p = t.prob[b];
   if (!t.active[p]) return;
+  const long long e = t.start[b] + (long long)blockIdx.y * blockDim.x + threadIdx.x;
+  if (e >= t.end[b]) return;
   const D4* tgt = args[p].tgt;
-  const long long base = bv.voff[p];
-  for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nparts; ++q) s += bv.partial[q * bv.pstride + e];
-    bv.out[e] = bv.mu[e] + tgt[(e - base) / 3].w * s;
-  }
+  double s = 0.0;
+  for (int q = 0; q < nparts; ++q) s += bv.partial[q * bv.pstride + e];
+  bv.out[e] = bv.mu[e] + tgt[(e - bv.voff[p]) / 3].w * s;
 }
 
 // ------------------------------------------------------------------ batched GEMV
@@ -1340,7 +1340,8 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
       pairs_dw_batch_kernel<1><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_active, bv, parts);
       if (parts > 1) {
         ++t_launches;
-        if (seg_ctas(seg) > 0) pair_parts_reduce_batch_kernel<<<seg_ctas(seg), 256, 0, st>>>(seg, args, bv, parts);
+        if (seg_ctas(seg) > 0)
+          pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), kSegChunkMax / 128), 128, 0, st>>>(seg, args, bv, parts);
       }
     }
   } else {
