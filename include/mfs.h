@@ -182,7 +182,8 @@ mfs_status mfs_set_background_flow(mfs_ctx* ctx, const double* U, const double* 
 mfs_status mfs_build(mfs_ctx* ctx, const mfs_params* params);
 mfs_status mfs_sizes(const mfs_ctx* ctx, mfs_sizes_t* out);
 
-/* Solve eq. resistance for the current boundary data, then form lambda = B^+ mu in FP64.
+/* Solve eq. resistance for the current boundary data, then form lambda = B^+ mu (FP64, or the
+ * double-float factors at ~2^-46 relative accuracy for MFS_MIXED).
  * NULL opts = defaults; info may be NULL.  MFS_ERR_NOT_CONVERGED still leaves the
  * best iterate's outputs available. */
 mfs_status mfs_solve(mfs_ctx* ctx, const mfs_solve_opts* opts, mfs_solve_info* info);

@@ -1163,8 +1163,15 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
   for (int p = 0; p < K; ++p) live[p] = 1;
   if ((s = set_active(R, live)) != MFS_OK) return s;
   timed(c0, c0->ev_gemv, [&] {
-    launch_gemv<double>(B->gA, B->x, B->tmp, R.st);
-    launch_gemv<double>(B->gV, B->tmp, B->lam, R.st);
+    if (o.precision == MFS_MIXED) {
+      // double-float factors (~2^-46 relative) instead of the FP64 pipes
+      launch_split_dw(B->n_total, B->x, B->x2, R.st);
+      launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
+      launch_gemv_dw(B->gV, B->t2, nullptr, B->lam, R.st);
+    } else {
+      launch_gemv<double>(B->gA, B->x, B->tmp, R.st);
+      launch_gemv<double>(B->gV, B->tmp, B->lam, R.st);
+    }
   });
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
@@ -1946,8 +1953,10 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
     }
     if (rel <= o.tol) converged = true;
   }
-  // lambda = B^+ mu in FP64, then forces and torques
+  // lambda = B^+ mu (double-float factors for MFS_MIXED, FP64 otherwise), then forces and torques
+  c->dw_pairs = (o.precision == MFS_MIXED);
   precond<double>(c, c->d_mu, c->d_lam);
+  c->dw_pairs = c->dw_fast_a = false;
   launch_forces_torques(c->src, c->d_lam, c->d_F, c->d_T, c->stream);
   if (c->mode == 1) {
     // rigid velocities from the border unknowns (V_k, Omega_k) per sphere

@@ -1102,12 +1102,16 @@ __global__ void batch_givens_kernel(GivensState S, int j, const double* __restri
       S.active[p] = 0;
       done = 1;
     } else {
-      col[j + 1] = hnext;
+      // earlier rotations; r carries the partly rotated entry down the column, so the dependent
+      // chain is one multiply-add per step while the loads of h, cs and sn run ahead of it
+      double r = col[0];
       for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
+        const double x = col[i + 1];
+        col[i] = cs[i] * r + sn[i] * x;
+        r = -sn[i] * r + cs[i] * x;
       }
+      col[j] = r;
+      col[j + 1] = hnext;
       const double den = hypot(col[j], col[j + 1]);
       const double c = den > 0 ? col[j] / den : 1.0, sj = den > 0 ? col[j + 1] / den : 0.0;
       csg[j] = c;
