@@ -195,6 +195,56 @@ def suspension_kernel_rates(device, fp32_peak):
     return out
 
 
+def batched_suspensions(device, n_problems=16, p_hi=8):
+    """Many small independent suspensions (P_i log-uniform in [2, p_hi], volume fraction
+    U(0.05, 0.3), gaps of attached spheres log-uniform in [1e-3, 1e-1]; N = 400, M0 = 800,
+    R_p = 0.63): one lockstep MIXED batch against the same problems solved one after another in
+    plain FP64, both at tol 1e-6, wall time including host synchronisation."""
+    import threading as th
+    from paper_2407_03343_gb300 import mfs, workloads
+    cents = workloads.batch(n_problems=n_problems, seed=5, p_lo=2, p_hi=p_hi)
+    ctxs = [mfs.Context(device) for _ in cents]
+    errs = []
+
+    def build(i):
+        try:
+            ctxs[i].set_spheres(cents[i])
+            ctxs[i].build(n_proxy=400, r_proxy=0.63, m_basic=800)
+        except Exception as e:  # surfaced below
+            errs.append(e)
+    t0 = time.perf_counter()
+    thr = [th.Thread(target=build, args=(i,)) for i in range(len(ctxs))]
+    [t.start() for t in thr]
+    [t.join() for t in thr]
+    if errs:
+        raise errs[0]
+    setup = time.perf_counter() - t0
+    for i, c in enumerate(ctxs):
+        v, w = workloads.rigid_velocities(cents[i].shape[0], seed=100 + i)
+        c.set_rigid_velocities(v, w)
+        c.set_profiling(True)
+        c.timing(reset=True)
+    t0 = time.perf_counter()
+    infos = mfs.batch_solve(ctxs, precision="mixed", tol=1e-6, allow_not_converged=True)
+    t_mixed = time.perf_counter() - t0
+    ft_mixed = [np.concatenate([a.ravel() for a in c.forces_torques()]) for c in ctxs]
+    pairs = sum(c.timing(reset=True).pair_interactions for c in ctxs)
+    t0 = time.perf_counter()
+    for c in ctxs:
+        c.solve(precision="fp64", tol=1e-6, allow_not_converged=True)
+    t_fp64 = time.perf_counter() - t0
+    ft_err = max(float(np.abs(a - np.concatenate([x.ravel() for x in c.forces_torques()])).max()
+                       / max(1e-300, np.abs(a).max())) for a, c in zip(ft_mixed, ctxs))
+    out = {"problems": len(ctxs), "spheres": int(sum(c.shape[0] for c in cents)),
+           "contacts": int(sum(workloads.count_near_contacts(c)[0] for c in cents)), "setup_s": setup,
+           "mixed_batch_s": t_mixed, "fp64_sequential_s": t_fp64, "speedup": t_fp64 / t_mixed,
+           "mixed_pairs_per_s": pairs / t_mixed, "converged": int(sum(i.converged for i in infos)),
+           "max_ft_diff_mixed_vs_fp64": ft_err}
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -418,6 +468,7 @@ def main():
                                       "avg_launch_us": 1000.0 * ms32 / max(1, sum(t.pair_launches for t in t32))}
         extras["cpu_baseline"] = oracle_sample(15.0)
         extras["pair_kernels_200_spheres"] = suspension_kernel_rates(local, fp32_peak)
+        extras["batched_suspensions"] = batched_suspensions(local)
 
     if rank == 0:
         line = {"metric": "Stokeslet pair-interactions/s", "value": value, "unit": "pair-interactions/s",
