@@ -711,6 +711,8 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
     B->seg.active = B->d_active;
     B->seg.list = B->d_cchunk;
     B->seg.nlist = 0;
+    B->seg.counter = B->alloc<unsigned>(K);
+    ok = ok && B->seg.counter && cudaMemset(B->seg.counter, 0, sizeof(unsigned) * K) == cudaSuccess;
   }
   const long long n = B->n_total;
   ok = ok && (B->wb = B->alloc<double>(n)) && (B->x = B->alloc<double>(n)) && (B->r = B->alloc<double>(n)) &&

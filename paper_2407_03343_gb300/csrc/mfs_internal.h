@@ -176,6 +176,8 @@ struct SegTable {
   const int* active = nullptr;
   const int* list = nullptr;    // optional: the chunks of the active problems (nlist of them); the
   int nlist = 0;                //   launches then cover only those
+  unsigned* counter = nullptr;  // optional, K zeros: the dot products are then reduced per problem by
+                                //   the last CTA of each problem instead of a second kernel
 };
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
                      double* h, cudaStream_t st);

@@ -1004,9 +1004,10 @@ constexpr int kSegChunkMax = 1024;
 constexpr int kSegDotVecs = 16;   // basis vectors per CTA
 constexpr int kSegUpdSub = 128;   // elements per CTA of the update (one per thread)
 __global__ void seg_dots_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
-                                const double* __restrict__ w, double* __restrict__ partial) {
+                                const double* __restrict__ w, double* __restrict__ partial, double* __restrict__ h) {
   const int b = seg_chunk(t);
-  if (!t.active[t.prob[b]]) return;
+  const int p = t.prob[b];
+  if (!t.active[p]) return;
   const long long lo = t.start[b];
   const int len = (int)(t.end[b] - lo);
   __shared__ double ws[kSegChunkMax];
@@ -1022,6 +1023,25 @@ __global__ void seg_dots_kernel(SegTable t, int nvec, const double* __restrict__
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if (lane == 0) partial[(long long)i * t.nchunks + b] = d;
   }
+  if (!t.counter) return;
+  // the last CTA of problem p to finish adds its partial dots in chunk order (so the result does
+  // not depend on which CTA that is) and re-arms the counter for the next launch
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned total = (unsigned)(t.pchunk[p + 1] - t.pchunk[p]) * gridDim.y;
+    last = atomicAdd(&t.counter[p], 1u) == total - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+    double sum = 0.0;
+    for (int c = t.pchunk[p]; c < t.pchunk[p + 1]; ++c) sum += __ldcg(&partial[(long long)i * t.nchunks + c]);
+    h[(long long)i * t.K + p] = sum;
+  }
+  if (threadIdx.x == 0) t.counter[p] = 0u;
 }
 
 // h[i K + p] = sum over problem p's chunks (in order) of the partial dots of vector i
@@ -1357,10 +1377,13 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,
                      double* h, cudaStream_t st) {
   if (seg_ctas(t) == 0 || nvec == 0) return;
-  t_launches += 2;
+  ++t_launches;
   seg_dots_kernel<<<dim3(seg_ctas(t), (nvec + kSegDotVecs - 1) / kSegDotVecs), kSegThreads, 0, st>>>(t, nvec, V, ldv,
-                                                                                                     w, partial);
-  seg_reduce_kernel<<<t.K, 128, 0, st>>>(t, nvec, partial, h);
+                                                                                                     w, partial, h);
+  if (!t.counter) {
+    ++t_launches;
+    seg_reduce_kernel<<<t.K, 128, 0, st>>>(t, nvec, partial, h);
+  }
 }
 void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
                        double* w, cudaStream_t st) {
