@@ -162,3 +162,26 @@ def test_translation_invariance_and_linearity():
     c12 = solve.forces_torques(d1, sys1.solve(v1 + 2 * v2, o1 + 2 * o2).lam)
     c2 = solve.forces_torques(d1, sys1.solve(v2, o2).lam)
     assert np.allclose(c12[0], a[0] + 2 * c2[0], atol=1e-8 * np.abs(c12[0]).max())
+
+
+def test_fixed_sphere_in_background_flow():
+    # a sphere held fixed in u_inf = U + w x (x - c) feels the flow as if it moved with -U and
+    # rotated with -w: F = -6 pi mu a U, T = -8 pi mu a^3 w (on the fluid); in a pure strain
+    # about its centre it exerts neither force nor torque
+    p = small(visc=0.7)
+    c = np.array([0.3, -0.2, 0.5])
+    d = geometry.build([c], 1.0, p)
+    U = np.array([0.4, -0.3, 0.8])
+    w = np.array([0.2, 0.5, -0.6])
+    zero = np.zeros((1, 3))
+    # rotation about the sphere's centre: w x (x - c) = w x x - w x c
+    bg = solve.Background(U=U - np.cross(w, c), omega=w)
+    sol = solve.solve_o2(d, zero, zero, bg)
+    F, T = solve.forces_torques(d, sol.lam)
+    assert np.allclose(F[0], -6 * math.pi * 0.7 * U, atol=1e-5 * 6 * math.pi * 0.7)
+    assert np.allclose(T[0], -8 * math.pi * 0.7 * w, atol=1e-5 * 8 * math.pi * 0.7)
+    E = np.array([[0.3, 0.2, 0.0], [0.2, -0.1, 0.4], [0.0, 0.4, -0.2]])   # symmetric, traceless
+    sol = solve.solve_o2(d, zero, zero, solve.Background(U=-E @ c, E=E))
+    F, T = solve.forces_torques(d, sol.lam)
+    scale = 6 * math.pi * 0.7 * np.abs(E).max()   # drag scale of the strain velocities
+    assert np.abs(F).max() < 1e-5 * scale and np.abs(T).max() < 1e-5 * scale
