@@ -185,3 +185,17 @@ def test_fixed_sphere_in_background_flow():
     F, T = solve.forces_torques(d, sol.lam)
     scale = 6 * math.pi * 0.7 * np.abs(E).max()   # drag scale of the strain velocities
     assert np.abs(F).max() < 1e-5 * scale and np.abs(T).max() < 1e-5 * scale
+
+
+def test_rotating_sphere_exterior_flow_is_exact_solution():
+    # rotating sphere: u = (a / r)^3 Omega x r
+    p = small()
+    a = 1.2
+    d = geometry.build([[0.0, 0.0, 0.0]], a, p)
+    W = np.array([[0.3, -0.8, 0.5]])
+    sol = solve.solve_o2(d, np.zeros((1, 3)), W)
+    x = np.array([[1.8, 0.3, -0.2], [0.0, 0.0, 3.0], [-2.5, 1.5, 1.0]])
+    u = solve.velocity(d, sol.lam, x)
+    r = np.linalg.norm(x, axis=1)[:, None]
+    exact = (a / r) ** 3 * np.cross(W, x)
+    assert np.allclose(u, exact, atol=2e-5 * np.abs(W).max())
