@@ -206,6 +206,7 @@ class Context:
 
     # -- problem set-up
     def set_spheres(self, centres, radius=1.0):
+        """P sphere centres (P, 3) of one common radius (mfs_set_spheres)."""
         c = _f64(centres).reshape(-1, 3)
         P = c.shape[0]
         r = _f64(np.broadcast_to(np.asarray(radius, dtype=np.float64), (P,)).copy())
@@ -213,20 +214,24 @@ class Context:
         self.P = P
 
     def build(self, params: Params | None = None, **kw):
+        """Discretise and factor the one-body blocks (mfs_build); keywords override the defaults."""
         p = params if params is not None else default_params(**kw)
         self._check(self._L.mfs_build(self._h, C.byref(p)))
 
     def sizes(self) -> Sizes:
+        """Node, source and unknown counts of the built discretisation (mfs_sizes)."""
         s = Sizes()
         self._check(self._L.mfs_sizes(self._h, C.byref(s)))
         return s
 
     def set_rigid_velocities(self, v, omega):
+        """Rigid velocities v and omega, each (P, 3): the next solve is the resistance problem."""
         v = _f64(v, (self.P, 3))
         w = _f64(omega, (self.P, 3))
         self._check(self._L.mfs_set_rigid_velocities(self._h, _dp(v), _dp(w)))
 
     def set_rigid_velocities_device(self, v_ptr: int, omega_ptr: int):
+        """As set_rigid_velocities, from device pointers of 3P doubles each."""
         self._check(self._L.mfs_set_rigid_velocities_device(self._h, C.c_void_p(v_ptr), C.c_void_p(omega_ptr)))
 
     def set_forces_torques(self, F, T):
@@ -243,6 +248,7 @@ class Context:
         return v, w
 
     def set_background_flow(self, U=None, E=None, Omega=None):
+        """Background flow U + E x + Omega x x (each term optional; no arguments clears it)."""
         a = _f64(U, (3,)) if U is not None else None
         b = _f64(E, (3, 3)) if E is not None else None
         c = _f64(Omega, (3,)) if Omega is not None else None
@@ -250,6 +256,7 @@ class Context:
 
     # -- solve and outputs
     def solve(self, opts: SolveOpts | None = None, allow_not_converged=False, **kw) -> SolveInfo:
+        """GMRES solve with refinement (mfs_solve); keywords override the default options."""
         o = opts if opts is not None else default_solve_opts(**kw)
         info = SolveInfo()
         allow = (-5,) if allow_not_converged else ()
@@ -257,21 +264,25 @@ class Context:
         return info
 
     def forces_torques(self):
+        """(F, T), each (P, 3): force and torque each sphere exerts on the fluid."""
         F = np.zeros((self.P, 3))
         T = np.zeros((self.P, 3))
         self._check(self._L.mfs_get_forces_torques(self._h, _dp(F), _dp(T)))
         return F, T
 
     def forces_torques_device(self, F_ptr: int, T_ptr: int):
+        """As forces_torques, into device buffers of 3P doubles each."""
         self._check(self._L.mfs_get_forces_torques_device(self._h, C.c_void_p(F_ptr), C.c_void_p(T_ptr)))
 
     def eval_velocity(self, x):
+        """Disturbance velocity u(x) at points x (n, 3), from the solved strengths."""
         x = _f64(x).reshape(-1, 3)
         u = np.zeros_like(x)
         self._check(self._L.mfs_eval_velocity(self._h, x.shape[0], _dp(x), _dp(u)))
         return u
 
     def strengths(self, with_positions=False):
+        """Source strengths lambda in the library order (optionally with positions and types)."""
         s = self.sizes()
         lam = np.zeros(s.n_unknowns)
         nv = s.n_unknowns // 3
@@ -281,6 +292,7 @@ class Context:
         return (lam, pos, typ) if with_positions else lam
 
     def source_layout(self):
+        """Positions (n_sources, 3) and types (0 Stokeslet, 1 rotlet, 2 dipole) of all vector sources."""
         s = self.sizes()
         nv = s.n_unknowns // 3
         pos = np.zeros((nv, 3))
@@ -289,6 +301,7 @@ class Context:
         return pos, typ
 
     def collocation(self):
+        """Collocation nodes (n, 3), area weights (n) and owner sphere (n)."""
         s = self.sizes()
         x = np.zeros((s.n_colloc, 3))
         w = np.zeros(s.n_colloc)
@@ -297,18 +310,21 @@ class Context:
         return x, w, o
 
     def rhs(self):
+        """Scaled boundary data W b at the collocation nodes (3 n)."""
         s = self.sizes()
         b = np.zeros(3 * s.n_colloc)
         self._check(self._L.mfs_get_rhs(self._h, _dp(b)))
         return b
 
     def apply_operator(self, mu, precision=FP64):
+        """G_hat mu (the preconditioned operator) in the given precision."""
         mu = _f64(mu)
         out = np.zeros_like(mu)
         self._check(self._L.mfs_apply_operator(self._h, int(precision), _dp(mu), _dp(out)))
         return out
 
     def apply_precond(self, mu, precision=FP64):
+        """lambda_hat = B^+ mu for every sphere (step 1)."""
         mu = _f64(mu)
         out = np.zeros(self.sizes().n_unknowns)
         self._check(self._L.mfs_apply_precond(self._h, int(precision), _dp(mu), _dp(out)))
@@ -319,14 +335,17 @@ class Context:
         self._check(self._L.mfs_apply_precond_noalloc(self._h, C.c_void_p(d_mu_ptr), C.c_void_p(d_lambda_hat_ptr)))
 
     def set_profiling(self, on=True):
+        """Record CUDA events around the pair and GEMV launches of this context."""
         self._check(self._L.mfs_set_profiling(self._h, 1 if on else 0))
 
     def timing(self, reset=False) -> Timing:
+        """Launch counts, device times and work counters since the last reset."""
         t = Timing()
         self._check(self._L.mfs_get_timing(self._h, C.byref(t), 1 if reset else 0))
         return t
 
     def apply_pairs(self, lam_hat, mu, precision=FP64):
+        """mu + W sum over other spheres of G lambda_hat (steps 2 and 3)."""
         lam_hat = _f64(lam_hat)
         mu = _f64(mu)
         out = np.zeros_like(mu)
