@@ -182,6 +182,18 @@ mfs_status mfs_set_background_flow(mfs_ctx* ctx, const double* U, const double* 
 mfs_status mfs_build(mfs_ctx* ctx, const mfs_params* params);
 mfs_status mfs_sizes(const mfs_ctx* ctx, mfs_sizes_t* out);
 
+/* The discretisation step of mfs_build alone (Sec. 2.1 basic grids, Sec. 2.3 image lines,
+ * Sec. 5.1 n_im rule, caps and weights), on the host, without a context or a GPU: P spheres of
+ * radius `radius` at `centres` (P*3), `params` NULL = defaults.  Call once with null arrays to
+ * get *n_colloc and *n_sources (vector sources; an image node counts 3), then with arrays of
+ * those sizes: x (n_colloc*3), w (n_colloc) and owner (n_colloc) in the layout of
+ * mfs_get_collocation, pos (n_sources*3) and type (n_sources) in that of mfs_get_strengths.
+ * Any pointer may be NULL.  Returns MFS_ERR_ARG for bad sizes or parameters and
+ * MFS_ERR_GEOMETRY for touching or overlapping spheres; nothing is allocated on a device. */
+mfs_status mfs_discretise_host(int P, const double* centres, double radius, const mfs_params* params,
+                               int* n_colloc, int* n_sources, double* x, double* w, int* owner,
+                               double* pos, int* type);
+
 /* Solve eq. resistance for the current boundary data, then form lambda = B^+ mu (FP64, or the
  * double-float factors at ~2^-46 relative accuracy for MFS_MIXED).
  * NULL opts = defaults; info may be NULL.  MFS_ERR_NOT_CONVERGED still leaves the

@@ -1743,6 +1743,43 @@ mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   return MFS_OK;
 }
 
+mfs_status mfs_discretise_host(int P, const double* centres, double radius, const mfs_params* params, int* n_colloc,
+                               int* n_sources, double* x, double* w, int* owner, double* pos, int* type) {
+  if (P < 1 || !centres || !(radius > 0) || !std::isfinite(radius)) return MFS_ERR_ARG;
+  for (int i = 0; i < 3 * P; ++i)
+    if (!std::isfinite(centres[i])) return MFS_ERR_ARG;
+  mfs_params p;
+  if (params) p = *params; else mfs_default_params(&p);
+  HostDisc d;
+  std::string err;
+  mfs_status s = build_discretisation(centres, P, radius, p, d, err);
+  if (s != MFS_OK) return s;
+  const int N = d.prm.n_proxy;
+  if (n_colloc) *n_colloc = d.n_colloc();
+  if (n_sources) *n_sources = P * N + 3 * d.n_img();
+  if (x) std::copy(d.colloc.begin(), d.colloc.end(), x);
+  if (w) std::copy(d.weight.begin(), d.weight.end(), w);
+  if (owner) std::copy(d.owner.begin(), d.owner.end(), owner);
+  if (pos || type) {
+    // the strength order of mfs_get_strengths: per sphere its proxies, then S, R, D per image node
+    long long v = 0;
+    for (int k = 0; k < P; ++k) {
+      for (int j = 0; j < N; ++j, ++v) {
+        if (pos)
+          for (int q = 0; q < 3; ++q) pos[3 * v + q] = d.centres[3 * k + q] + d.proxy_rel[3 * j + q];
+        if (type) type[v] = 0;
+      }
+      for (int j = d.img_off[k]; j < d.img_off[k + 1]; ++j)
+        for (int t = 0; t < 3; ++t, ++v) {
+          if (pos)
+            for (int q = 0; q < 3; ++q) pos[3 * v + q] = d.image[3 * j + q];
+          if (type) type[v] = t;
+        }
+    }
+  }
+  return MFS_OK;
+}
+
 mfs_status mfs_sizes(const mfs_ctx* cc, mfs_sizes_t* out) {
   mfs_ctx* c = const_cast<mfs_ctx*>(cc);
   if (!c || !out) return MFS_ERR_ARG;

@@ -98,6 +98,7 @@ def lib():
         "mfs_set_background_flow": (C.c_int, [P, _D, _D, _D]),
         "mfs_build": (C.c_int, [P, C.POINTER(Params)]),
         "mfs_sizes": (C.c_int, [P, C.POINTER(Sizes)]),
+        "mfs_discretise_host": (C.c_int, [C.c_int, _D, C.c_double, C.POINTER(Params), _I, _I, _D, _D, _I, _D, _I]),
         "mfs_solve": (C.c_int, [P, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
         "mfs_get_forces_torques": (C.c_int, [P, _D, _D]),
         "mfs_get_forces_torques_device": (C.c_int, [P, P, P]),
@@ -351,6 +352,29 @@ class Context:
         out = np.zeros_like(mu)
         self._check(self._L.mfs_apply_pairs(self._h, int(precision), _dp(lam_hat), _dp(mu), _dp(out)))
         return out
+
+
+def discretise_host(centres, radius=1.0, params: Params | None = None, **kw):
+    """The discretisation of build() computed on the host without a GPU: returns the collocation
+    nodes (n, 3), weights (n), owners (n), source positions (m, 3) and types (m)."""
+    L = lib()
+    c = _f64(centres).reshape(-1, 3)
+    p = params if params is not None else default_params(**kw)
+    nc, ns = C.c_int(0), C.c_int(0)
+    st = L.mfs_discretise_host(c.shape[0], _dp(c), float(radius), C.byref(p), C.byref(nc), C.byref(ns),
+                               None, None, None, None, None)
+    if st != 0:
+        raise MfsError(st, "mfs_discretise_host failed")
+    x = np.zeros((nc.value, 3))
+    w = np.zeros(nc.value)
+    owner = np.zeros(nc.value, dtype=np.int32)
+    pos = np.zeros((ns.value, 3))
+    typ = np.zeros(ns.value, dtype=np.int32)
+    st = L.mfs_discretise_host(c.shape[0], _dp(c), float(radius), C.byref(p), None, None, _dp(x), _dp(w), _ip(owner),
+                               _dp(pos), _ip(typ))
+    if st != 0:
+        raise MfsError(st, "mfs_discretise_host failed")
+    return x, w, owner, pos, typ
 
 
 def batch_solve(contexts, opts: SolveOpts | None = None, allow_not_converged=False, **kw):
