@@ -87,6 +87,10 @@ typedef struct {
   int build_factors;    /* 1 (default): compute the one-body pseudo-inverses; 0: discretise only, after
                            which mfs_apply_pairs and mfs_eval_velocity work but solves and the
                            pseudo-inverse steps return MFS_ERR_STATE */
+  int nim_min;          /* at least this n_im for every contact with delta < nim_cut (default 0: the rule as
+                           printed, eq. image_est).  Not in the paper: with nim_cut 0.3 and nim_min 2 the
+                           gaps 0.15 <= delta < 0.3, where the printed rule places no images and the coarse
+                           proxy sphere alone misses the 1e-3 target, get two images each */
 } mfs_params;
 
 /* GMRES / refinement options (precision as above).  Every mode re-evaluates the residual

@@ -54,6 +54,7 @@ class Params:
     nim_cut: float = 0.15
     nim_max: int = 20
     nim_fixed: int = -1           # >= 0 forces n_im for every contact with gap < nim_cut
+    nim_min: int = 0              # lower bound on n_im below nim_cut (0: eq. image_est as printed)
     left_precond: int = 1         # row scaling W (Sec. 5.1 remark left-precond)
     visc: float = 1.0             # viscosity mu
     n_check: int = 500            # check points per sphere for eps_res (Sec. 4)
@@ -103,7 +104,7 @@ def n_images(delta: float, p: Params) -> int:
         return 0
     if p.nim_fixed >= 0:
         return int(p.nim_fixed)
-    n = math.ceil(-p.nim_a * math.log10(delta) - p.nim_b)
+    n = max(math.ceil(-p.nim_a * math.log10(delta) - p.nim_b), p.nim_min)
     return int(min(max(n, 0), p.nim_max))
 
 

@@ -1256,6 +1256,7 @@ void mfs_default_params(mfs_params* p) {
   p->left_precond = 1;
   p->visc = 1.0;
   p->build_factors = 1;
+  p->nim_min = 0;
 }
 
 void mfs_default_solve_opts(mfs_solve_opts* o) {

@@ -41,6 +41,7 @@ int image_count(double delta, const mfs_params& p) {
   if (delta >= p.nim_cut) return 0;
   if (p.nim_fixed >= 0) return p.nim_fixed;
   double v = std::ceil(-p.nim_a * std::log10(delta) - p.nim_b);
+  if (v < p.nim_min) v = p.nim_min;
   if (v < 0) v = 0;
   if (v > p.nim_max) v = p.nim_max;
   return (int)v;
@@ -63,7 +64,7 @@ void perp_frame(const double* e, double* e1, double* e2) {
 mfs_status build_discretisation(const double* centres, int P, double a, const mfs_params& p,
                                 HostDisc& out, std::string& err) {
   if (P <= 0 || p.n_proxy <= 0 || p.m_basic <= 0 || !(a > 0) || !(p.r_proxy > 0) || p.r_proxy >= 1.0 ||
-      p.alpha1 < 0 || p.alpha2 < 0 || !(p.visc > 0) || p.nim_max < 0) {
+      p.alpha1 < 0 || p.alpha2 < 0 || !(p.visc > 0) || p.nim_max < 0 || p.nim_min < 0 || p.nim_min > p.nim_max) {
     err = "invalid discretisation parameters";
     return MFS_ERR_ARG;
   }

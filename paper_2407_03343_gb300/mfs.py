@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("beta1", C.c_double), ("beta2", C.c_double), ("eps_trunc", C.c_double),
                 ("nim_a", C.c_double), ("nim_b", C.c_double), ("nim_cut", C.c_double),
                 ("nim_max", C.c_int), ("nim_fixed", C.c_int), ("left_precond", C.c_int),
-                ("visc", C.c_double), ("build_factors", C.c_int)]
+                ("visc", C.c_double), ("build_factors", C.c_int), ("nim_min", C.c_int)]
 
 
 class SolveOpts(C.Structure):

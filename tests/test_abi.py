@@ -26,6 +26,7 @@ def test_struct_layouts_match_defaults(L):
     assert p.n_proxy == 686 and abs(p.r_proxy - 0.63) < 1e-15 and p.m_basic == 823
     assert p.alpha1 == 6 and p.alpha2 == 6 and p.nim_max == 20 and p.nim_fixed == -1
     assert abs(p.eps_trunc - 5e-12) < 1e-25 and abs(p.nim_a - 8.72) < 1e-15 and abs(p.visc - 1.0) < 1e-15
+    assert p.build_factors == 1 and p.nim_min == 0
     o = mfs.default_solve_opts()
     assert o.precision == mfs.MIXED and abs(o.tol - 1e-6) < 1e-20 and o.restart == 300
     assert o.max_iter == 2000 and o.max_refine == 20 and o.residual == mfs.RESIDUAL_AUTO

@@ -15,6 +15,8 @@ CASES = {
     "tetrahedron, gap 1e-3": (workloads.tetrahedron(1e-3), dict(n_proxy=686, r_proxy=0.63, m_basic=823)),
     "cluster of 20": (workloads.cluster(20, 1e-3, seed=2), dict(n_proxy=686, r_proxy=0.63, m_basic=823)),
     "suspension of 40": (workloads.suspension(40, 0.2, seed=3), dict(n_proxy=400, r_proxy=0.63, m_basic=800)),
+    "minimum images below gap 0.3": (workloads.tetrahedron(0.2), dict(n_proxy=400, r_proxy=0.63, m_basic=800,
+                                                                       nim_cut=0.3, nim_min=2)),
 }
 
 

@@ -50,6 +50,10 @@ def test_image_count_rule():
     assert g.n_images(1e-3, p) == 20          # 20.01 -> 21, capped at 20 (Sec. 5.1 text)
     q = g.Params(nim_fixed=10)
     assert g.n_images(0.1, q) == 10 and g.n_images(0.2, q) == 0
+    # opt-in lower bound (not in the paper): applies below nim_cut only, the rule still wins above it
+    m = g.Params(nim_cut=0.3, nim_min=2)
+    assert g.n_images(0.2, m) == 2 and g.n_images(0.29, m) == 2 and g.n_images(0.3, m) == 0
+    assert g.n_images(0.1, m) == 3 and g.n_images(1e-2, m) == 12
 
 
 def test_image_radii_half_chebyshev():

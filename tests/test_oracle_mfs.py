@@ -199,3 +199,18 @@ def test_rotating_sphere_exterior_flow_is_exact_solution():
     r = np.linalg.norm(x, axis=1)[:, None]
     exact = (a / r) ** 3 * np.cross(W, x)
     assert np.allclose(u, exact, atol=2e-5 * np.abs(W).max())
+
+
+def test_minimum_images_close_the_image_free_window():
+    # at gap 0.2 the printed rule places no images and the coarse proxy sphere alone misses the
+    # 1e-3 residual target; two images per sphere bring it below (plain least squares, O1)
+    kw = dict(n_proxy=686, r_proxy=0.63, m_basic=823)
+    rng = np.random.default_rng(2)
+    v, w = rng.normal(size=(2, 3)), rng.normal(size=(2, 3))
+    c = workloads.two_spheres(0.2)
+    d0 = geometry.build(c, 1.0, geometry.Params(**kw))
+    d2 = geometry.build(c, 1.0, geometry.Params(nim_cut=0.3, nim_min=2, **kw))
+    assert sum(s.image.shape[0] for s in d0.spheres) == 0 and all(s.image.shape[0] == 2 for s in d2.spheres)
+    e0 = solve.residual_max(d0, solve.solve_o1(d0, v, w).lam, v, w)
+    e2 = solve.residual_max(d2, solve.solve_o1(d2, v, w).lam, v, w)
+    assert e0 > 3e-3 and e2 < 5e-4
