@@ -89,3 +89,13 @@ def test_random_cluster_of_twenty():
     assert info.converged
     # the paper reaches 1e-3; measured here 1.7e-3 (seed 2) and 4.2e-3 (seed 1)
     assert er < 1e-2
+
+
+def test_minimum_images_close_the_image_free_window():
+    # gap 0.2: the printed rule places no images and the coarse grid misses 1e-3; the opt-in
+    # minimum of two images per contact below gap 0.3 brings the residual well below it
+    c = workloads.two_spheres(0.2)
+    v, w = workloads.rigid_velocities(2, seed=2)
+    _, _, _, er_rule = solve(c, v, w, **COARSE)
+    _, _, _, er_min = solve(c, v, w, nim_cut=0.3, nim_min=2, **COARSE)
+    assert er_rule > 3e-3 and er_min < 5e-4
