@@ -6,7 +6,8 @@ log-spaced in [1e-3, 1], three relative motions each (squeezing, shearing, count
 N = 800 proxy Stokeslets on R_p = 0.63, M0 = 1600 basic collocation nodes, images and caps by
 the n_im rule (<= 20 per contact, <= 60 image sources), one-body truncation 5e-12, GMRES
 tolerance 1e-6.  One step = the 54 resistance solves (steps 1-3 of the preconditioned apply
-inside GMRES, FP64 residual, lambda = B^+ mu, forces and torques), all 54 in one lockstep batch
+inside GMRES, the refinement residual with the double-float operator at this tolerance,
+lambda = B^+ mu, forces and torques), all 54 in one lockstep batch
 in which the three motions of a geometry share its factor reads; the 18 discretisations and
 their one-body SVDs are built once before timing (reported as setup_s).
 
@@ -27,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU baseline reports the cores it uses: keep numpy's BLAS to one thread (set before import)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
