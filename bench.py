@@ -28,20 +28,22 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the CPU baseline reports the cores it uses: keep numpy's BLAS to one thread (set before import)
-for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
 N_PROXY, R_PROXY, M_BASIC = 800, 0.63, 1600
 MOTIONS = ("squeeze", "shear", "rotate")
-# Algorithmic work per pair, counted from the kernels' source (see the design notes):
-# FP32 pair math: 28 flops per Stokeslet pair, 63 per S+R+D image triple (FMA = 2).
-# Double-float (compensated) evaluation of the same math on the FP32 pipes: 248 FP32 flops
-# (204 instructions, 44 of them FMAs) per Stokeslet pair and 544 (436, 108 FMAs) per image
-# triple, counted from the kernel source.
-FLOPS = {"fp32": (28.0, 63.0), "mixed": (248.0, 544.0)}
+SWEEP_TOL = 1e-6          # GMRES tolerance of the timed solves (Sec. 3, Sec. 5)
+SWEEP_RESTART = 300
+GOLDEN = os.path.join(ROOT, "tests", "golden", "gap_sweep_oracle.json")
+# Algorithmic work per pair (FMA = 2 flops, rsqrt = 1): 28 flops per Stokeslet pair and 63 per
+# S+R+D image triple at one node (shared distance and 1/r).  This is what `frac` is measured in.
+FLOPS_ALG = (28.0, 63.0)
+# FP32-pipe operations the double-float (compensated) kernel issues for the same pair math,
+# counted from its source: 248 per Stokeslet pair (204 instructions, 44 of them FMAs) and 544
+# per image triple (436, 108 FMAs).  Their rate against the FP32 peak is `issue_frac`, a
+# measure of how busy the pipes are, not of algorithmic throughput.
+FLOPS_ISSUED_DW = (248.0, 544.0)
 # dram__bytes_read.sum + dram__bytes_write.sum of one pairs_dw_batch_kernel<1> launch over the 18
 # gap-sweep problems (ncu --set full on `bench.py --kernel-case 20`; 5.05 MB read, 0 written):
 # the kernel is FP32-issue-bound and its operands stay in L2
@@ -56,7 +58,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 sweep and FP32 kernel side runs")
-    ap.add_argument("--restart", type=int, default=300, help="GMRES restart length of the timed solves")
+    ap.add_argument("--restart", type=int, default=SWEEP_RESTART, help="GMRES restart length of the timed solves")
+    ap.add_argument("--tol", type=float, default=SWEEP_TOL, help="GMRES tolerance of the timed solves")
     ap.add_argument("--kernel-case", type=int, default=0,
                     help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
     return ap.parse_args()
@@ -70,7 +73,7 @@ def workload_config(args):
     from paper_2407_03343_gb300 import workloads
     return {"workload": "gap sweep: 2 unit spheres x 18 gaps in [1e-3, 1] x 3 motions (54 resistance solves)",
             "n_proxy": N_PROXY, "r_proxy": R_PROXY, "m_basic": M_BASIC, "n_im": "rule, <= 20",
-            "eps_trunc": 5e-12, "gmres_tol": 1e-6, "gmres_restart": args.restart, "precision": args.precision,
+            "eps_trunc": 5e-12, "gmres_tol": args.tol, "gmres_restart": args.restart, "precision": args.precision,
             "gaps": [float(g) for g in workloads.gap_sweep_gaps()],
             "l2": "256 MB write between timed steps; resident factors ~5 GB exceed L2"}
 
@@ -127,9 +130,18 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle baseline
+def host_cores():
+    """Threads numpy's BLAS may use: the environment's setting if any, else every host core."""
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
 def oracle_sample(seconds_budget=20.0):
     """Step 2 of the oracle's preconditioned apply (off-diagonal target-from-source blocks built
-    and applied, as the oracle does it) for the delta = 1e-3 problem of the sweep."""
+    and applied, as the oracle does it) for the delta = 1e-3 problem of the sweep, numpy FP64
+    with its BLAS on all host cores."""
     from oracle import geometry, solve
     from paper_2407_03343_gb300 import workloads
     delta = workloads.gap_sweep_gaps()[0]
@@ -150,9 +162,28 @@ def oracle_sample(seconds_budget=20.0):
         el = time.perf_counter() - t0
         if el > seconds_budget or reps >= 50:
             break
-    return {"value": pairs * reps / el, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+    return {"value": pairs * reps / el, "unit": "pair-interactions/s", "cores": host_cores(), "kind": "oracle",
             "sample": f"oracle step-2 apply (off-diagonal blocks built in numpy FP64 and applied) of the "
                       f"delta=1e-3 two-sphere problem, {pairs} pairs per apply, {reps} applies in {el:.1f} s"}
+
+
+def oracle_solve_sample():
+    """One full oracle solve of a sweep problem (matrix-free GMRES on eq. resistance with the
+    three-step apply, O3) at the benchmark's tolerance, timed on the host: the delta = 0.0582
+    shear problem (images on both spheres).  Set-up (the two one-body SVDs) timed separately."""
+    from oracle import geometry, solve
+    from paper_2407_03343_gb300 import workloads
+    gap = workloads.gap_sweep_gaps()[9]
+    t0 = time.perf_counter()
+    d = geometry.build(workloads.two_spheres(gap), 1.0, geometry.Params(n_proxy=N_PROXY, r_proxy=R_PROXY,
+                                                                        m_basic=M_BASIC))
+    op = solve.Operator(d)
+    t1 = time.perf_counter()
+    v, w = workloads.motion("shear")
+    sol = solve.solve_o3(d, v, w, op=op, tol=SWEEP_TOL)
+    t2 = time.perf_counter()
+    return {"problem": f"gap {gap:.4g}, shear", "setup_s": t1 - t0, "solve_s": t2 - t1, "iters": sol.iters,
+            "cores": host_cores()}
 
 
 def reduce_over_ranks(total_ms, pairs, device):
@@ -182,8 +213,8 @@ def suspension_kernel_rates(device, fp32_peak):
     mu = np.zeros(3 * s.n_colloc)
     ctx.set_profiling(True)
     out = {"pairs_per_launch": s.pairs_fp, "contacts": s.n_contacts, "nodes": s.n_colloc}
-    for name, prec, fl in (("fp32", mfs.FP32, (28.0, 63.0)), ("double_float", mfs.MIXED, FLOPS["mixed"]),
-                           ("fp64", mfs.FP64, (28.0, 63.0))):
+    for name, prec in (("fp32", mfs.FP32), ("double_float", mfs.MIXED), ("fp64", mfs.FP64)):
+        fl = FLOPS_ALG
         ctx.apply_pairs(lam, mu, prec)   # warm-up
         ctx.timing(reset=True)
         reps = 3 if prec != mfs.FP64 else 1
@@ -195,6 +226,9 @@ def suspension_kernel_rates(device, fp32_peak):
         out[name] = {"ms_per_launch": 1000 * sec, "pairs_per_s": s.pairs_fp / sec, "tflops": flops / sec / 1e12,
                      "frac_of_fp32_peak": flops / sec / 1e12 / fp32_peak if prec != mfs.FP64 else None,
                      "frac_of_fp64_peak": flops / sec / 1e12 / 1.0 if prec == mfs.FP64 else None}
+        if prec == mfs.MIXED:
+            issued = (t.pair_proxy * FLOPS_ISSUED_DW[0] + t.pair_image_nodes * FLOPS_ISSUED_DW[1]) / t.pair_launches
+            out[name]["issue_frac"] = issued / sec / 1e12 / fp32_peak
     ctx.close()
     return out
 
@@ -247,6 +281,40 @@ def batched_suspensions(device, n_problems=16, p_hi=8):
     for c in ctxs:
         c.close()
     return out
+
+
+def sweep_accuracy(ctxs, d_F, d_T, probs):
+    """Errors of the last solved sweep against the oracle's solutions stored by
+    tests/golden/make_gap_sweep_oracle.py (O3 to 1e-9): the force/torque error of every one of
+    the 54 problems, max |F - F_o|, |T - T_o| over the problem's 12 components relative to the
+    largest of them, and the surface-velocity error at the stored check points of the problems
+    each context still holds (its last right-hand side), max |u - u_o| relative to max |u_o|.
+    Computed outside the timed region."""
+    import torch
+    if not os.path.exists(GOLDEN):
+        return {"error": "oracle values missing: " + os.path.relpath(GOLDEN, ROOT)}
+    gold = json.load(open(GOLDEN))
+    ng = len(ctxs)
+    ft_err, u_err = [], []
+    torch.cuda.synchronize()
+    for i, c in enumerate(probs):
+        g = gold["geometries"][i % ng]["problems"][i // ng]
+        F, T = d_F[i].cpu().numpy(), d_T[i].cpu().numpy()
+        Fo, To = np.array(g["F"]), np.array(g["T"])
+        ref = max(np.abs(Fo).max(), np.abs(To).max())
+        ft_err.append(max(np.abs(F - Fo).max(), np.abs(T - To).max()) / ref)
+    last = len(MOTIONS) - 1
+    for gi, c in enumerate(ctxs):
+        geo = gold["geometries"][gi]
+        x = np.array(geo["check_points"])
+        uo = np.array(geo["problems"][last]["u"])
+        u = c.eval_velocity(x)
+        u_err.append(float(np.abs(u - uo).max() / np.abs(uo).max()))
+    return {"ft_rel_err_max": float(max(ft_err)), "ft_rel_err_median": float(statistics.median(ft_err)),
+            "ft_problems": len(ft_err), "u_rel_err_max": float(max(u_err)), "u_problems": len(u_err),
+            "u_points_per_problem": int(np.array(gold["geometries"][0]["check_points"]).shape[0]),
+            "targets": {"u": 1e-3, "ft": 1e-5},
+            "oracle": "O3 matrix-free GMRES on eq. resistance to 1e-9 (tests/golden/gap_sweep_oracle.json)"}
 
 
 def run_reference(args):
@@ -309,17 +377,17 @@ def main():
     sizes = [c.sizes() for c in ctxs]
 
     prec = args.precision
-    opts = mfs.default_solve_opts(precision=prec, tol=1e-6, restart=args.restart)
+    opts = mfs.default_solve_opts(precision=prec, tol=args.tol, restart=args.restart)
+    vel = {m: workloads.motion(m) for m in MOTIONS}
     if args.kernel_case:
-        v, w = workloads.motion("squeeze")
-        for c in ctxs:
-            c.set_rigid_velocities(v, w)
-        mfs.batch_solve(ctxs, mfs.default_solve_opts(precision=prec, tol=1e-12, max_iter=args.kernel_case,
-                                                     max_refine=1), allow_not_converged=True)
+        # the benchmark's 54-problem batch, cut off after this many GMRES iterations
+        kprobs = [c for _ in MOTIONS for c in ctxs]
+        kvel = [vel[m] for m in MOTIONS for _ in ctxs]
+        mfs.batch_solve_rhs(kprobs, kvel, mfs.default_solve_opts(precision=prec, tol=1e-12, max_iter=args.kernel_case,
+                                                                 max_refine=1), allow_not_converged=True)
         torch.cuda.synchronize()
         print(json.dumps({"kernel_case": args.kernel_case, "setup_s": setup_s}))
         return 0
-    vel = {m: workloads.motion(m) for m in MOTIONS}
     dev = torch.device("cuda", local)
     d_vel = {m: (torch.tensor(v, dtype=torch.float64, device=dev), torch.tensor(w, dtype=torch.float64, device=dev))
              for m, (v, w) in vel.items()}
@@ -389,6 +457,8 @@ def main():
     gemv_ms = sum(t.gemv_ms for t in tms)
     gemv_bytes = sum(t.gemv_bytes for t in tms)
     gemv_launches = sum(t.gemv_launches for t in tms)
+    krylov_ms = sum(t.krylov_ms for t in tms)
+    krylov_bytes = sum(t.krylov_bytes for t in tms)
 
     # max over ranks of the timed region, pairs summed over ranks (weak scaling: every rank
     # solves its own sweep, no data-path collective)
@@ -396,13 +466,15 @@ def main():
     value = pairs_all / (total_ms_max / 1000.0)
 
     # ---- roofline of the dominant kernel (pair kernel), from its own launch events:
-    # algorithmic flops = proxy pairs x flops per Stokeslet pair + image node-pairs x flops per
-    # S+R+D triple, counted by the library for every pair launch in the timed steps
+    # algorithmic flops = proxy pairs x 28 + image node-pairs x 63, counted by the library for
+    # every pair launch in the timed steps, over the device time of those launches
     kind = 1 if prec == "mixed" else 0   # MFS_MIXED or MFS_FP64 pair kernel
-    fp_s, fp_i = FLOPS["mixed"] if prec == "mixed" else (28.0, 63.0)
     k_ms = sum(t.by_kind_ms[kind] for t in tms)
     k_launch = sum(t.by_kind_launches[kind] for t in tms)
-    alg_flops = sum(t.by_kind_proxy[kind] * fp_s + t.by_kind_image_nodes[kind] * fp_i for t in tms)
+    k_proxy = sum(t.by_kind_proxy[kind] for t in tms)
+    k_image = sum(t.by_kind_image_nodes[kind] for t in tms)
+    alg_flops = k_proxy * FLOPS_ALG[0] + k_image * FLOPS_ALG[1]
+    issued_flops = k_proxy * FLOPS_ISSUED_DW[0] + k_image * FLOPS_ISSUED_DW[1]
     achieved_tflops = alg_flops / (k_ms / 1000.0) / 1e12 if k_ms > 0 else 0.0
     fp64_refine = {"launches": sum(t.by_kind_launches[0] for t in tms), "ms": sum(t.by_kind_ms[0] for t in tms)}
     peaks = {}
@@ -411,21 +483,46 @@ def main():
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * (clocks["sm_mhz"] or sm_max) * 1e6 / 1e12  # FP32 FMA lanes x clock under load
-    roofline = {"bound": "alu", "kernel": "pairs_dw_kernel" if prec == "mixed" else "pairs_kernel<double>",
-                "achieved": achieved_tflops, "peak": fp32_peak if prec == "mixed" else 1.0,
-                "unit": "TFLOP/s", "frac": achieved_tflops / (fp32_peak if prec == "mixed" else 1.0),
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_mhz = clocks["sm_mhz"] or sm_max
+    # FP32 FMA lanes x 2 flops x the median SM clock sampled under load (152 SMs x 128 lanes)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    probe = {}
+    try:
+        p32, ms32p = mfs.probe_alu_peak(local, "fp32")
+        p64, ms64p = mfs.probe_alu_peak(local, "fp64")
+        probe = {"fp32_ffma_tflops": p32, "fp64_dfma_tflops": p64, "launch_ms": [ms32p, ms64p]}
+    except Exception as e:  # measured peak is context only; the roofline uses the derived one
+        probe = {"error": str(e)}
+    fp64_peak = probe.get("fp64_dfma_tflops") or 1.0
+    peak = fp32_peak if prec == "mixed" else fp64_peak
+    roofline = {"bound": "alu", "kernel": "pairs_dw_batch_kernel" if prec == "mixed" else "pairs_batch_kernel<double>",
+                "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s", "frac": achieved_tflops / peak,
+                "flops_per_unit": {"stokeslet_pair": FLOPS_ALG[0], "image_triple": FLOPS_ALG[1]},
+                "units_per_launch": {"proxy_pairs": k_proxy / max(k_launch, 1),
+                                     "image_node_pairs": k_image / max(k_launch, 1)},
                 # dram read + write of one captured launch (ncu, 18 gap-sweep problems, see profiles/)
                 "traffic": PAIR_DW_TRAFFIC_BYTES if prec == "mixed" else None,
                 "traffic_launch": "pairs_dw_batch_kernel<1>, 18-problem launch of --kernel-case 20"
                 if prec == "mixed" else None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock under load"
-                if prec == "mixed" else "FP64 DFMA measured 1.0 TFLOP/s",
+                if prec == "mixed" else "FP64 DFMA probe (mfs_probe_alu_peak)",
+                "peak_probe": probe,
                 "avg_launch_us": 1000.0 * k_ms / max(k_launch, 1),
                 "share_of_step": k_ms / total_ms if total_ms > 0 else None,
-                "fp64_refinement_pair_launches": fp64_refine,
-                "gemv_GBps": gemv_bytes / (gemv_ms / 1000.0) / 1e9 if gemv_ms > 0 else None,
-                "gemv_share_of_step": gemv_ms / total_ms if total_ms > 0 else None}
+                "fp64_refinement_pair_launches": fp64_refine}
+    if prec == "mixed":
+        # FP32-pipe operations actually issued by the compensated double-float evaluation
+        roofline["issue_frac"] = issued_flops / (k_ms / 1000.0) / 1e12 / fp32_peak if k_ms > 0 else None
+    gemv = {"GBps": gemv_bytes / (gemv_ms / 1000.0) / 1e9 if gemv_ms > 0 else None,
+            "frac_of_hbm": gemv_bytes / (gemv_ms / 1000.0) / 1e9 / hbm_peak if gemv_ms > 0 else None,
+            "share_of_step": gemv_ms / total_ms if total_ms > 0 else None, "launches": gemv_launches,
+            "bytes": "factor bytes read: Sigma^+ U^T (FP32 in the passes, hi/lo pairs in residuals) and V (hi/lo)"}
+    krylov = {"GBps": krylov_bytes / (krylov_ms / 1000.0) / 1e9 if krylov_ms > 0 else None,
+              "frac_of_hbm": krylov_bytes / (krylov_ms / 1000.0) / 1e9 / hbm_peak if krylov_ms > 0 else None,
+              "share_of_step": krylov_ms / total_ms if total_ms > 0 else None,
+              "bytes": "(4j + 10) n doubles per Arnoldi step j: two dot-product and two update launches of CGS2"}
+    accuracy = sweep_accuracy(ctxs, d_F, d_T, probs) if rank == 0 else None
 
     # ---- end to end through host buffers
     e2e_ms = []
@@ -444,19 +541,26 @@ def main():
 
     extras = {}
     if not args.no_extras and rank == 0:
-        # plain FP64 GPU solve of the same sweep (the comparison of the metric's second part)
-        o64 = mfs.default_solve_opts(precision="fp64", tol=1e-6)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mfs.batch_solve_rhs(probs, vel_host, o64)
-        t64 = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        mfs.batch_solve_rhs(probs, vel_host, opts)
-        tmix = time.perf_counter() - t0
+        # plain FP64 GPU solve of the same sweep against the mixed one (the metric's second part),
+        # each timed with CUDA events over repeats, both checked against the oracle
+        o64 = mfs.default_solve_opts(precision="fp64", tol=args.tol, restart=args.restart)
+        solve_ms = {}
+        for name, o, reps in (("fp64", o64, 2), ("mixed", opts, 5)):
+            ts = []
+            for _ in range(reps):
+                flush.fill_(1.0)
+                t, _ = timed_step(lambda: mfs.batch_solve_rhs_device(probs, v_ptrs, w_ptrs, F_ptrs, T_ptrs, o))
+                ts.append(t)
+            solve_ms[name] = ts
+            if name == "fp64":
+                acc64 = sweep_accuracy(ctxs, d_F, d_T, probs)
         for c in ctxs:
             c.timing(reset=True)
-        extras["sweep_solve_s"] = {"fp64": t64, "mixed": tmix, "speedup": t64 / tmix if tmix > 0 else None,
-                                   "tol": 1e-6}
+        m64, mmix = statistics.median(solve_ms["fp64"]), statistics.median(solve_ms["mixed"])
+        extras["sweep_solve_s"] = {"fp64": m64 / 1000.0, "mixed": mmix / 1000.0, "speedup": m64 / mmix,
+                                   "tol": args.tol, "repeats": {k: len(v) for k, v in solve_ms.items()},
+                                   "timing": "CUDA events on the launching stream, median of the repeats",
+                                   "accuracy_fp64": acc64}
         # FP32 pair kernel on the same problems (inner solves of the FP32 mode, 30 iterations each)
         o32 = mfs.default_solve_opts(precision="fp32", tol=1e-6, max_iter=30, max_refine=1)
         for c in ctxs:
@@ -471,6 +575,7 @@ def main():
                                       "frac_of_fp32_peak": (fl32 / (ms32 / 1000.0) / 1e12) / fp32_peak if ms32 else None,
                                       "avg_launch_us": 1000.0 * ms32 / max(1, sum(t.pair_launches for t in t32))}
         extras["cpu_baseline"] = oracle_sample(15.0)
+        extras["oracle_solve"] = oracle_solve_sample()
         extras["pair_kernels_200_spheres"] = suspension_kernel_rates(local, fp32_peak)
         extras["batched_suspensions"] = batched_suspensions(local)
 
@@ -480,7 +585,7 @@ def main():
                 "ms_per_step": total_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64 (pair sums double-float on FP32 pipes)" if prec == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(args),
-                "roofline": roofline, "clocks": clocks,
+                "roofline": roofline, "gemv": gemv, "krylov": krylov, "accuracy": accuracy, "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": "pair-interactions/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
                 "gpu_launches": launches, "setup_s": setup_s,

@@ -155,7 +155,9 @@ const char* mfs_last_error(const mfs_ctx* ctx);
  * (MFS_ERR_GEOMETRY).  Invalidates any previous build. */
 mfs_status mfs_set_spheres(mfs_ctx* ctx, int P, const double* centres, const double* radii);
 
-/* Rigid-body boundary data of eq. bc: v (P*3), omega (P*3). */
+/* Rigid-body boundary data of eq. bc: v (P*3), omega (P*3).  Non-finite values give MFS_ERR_ARG
+ * (the host variant checks them; device data that is not finite makes the next solve return
+ * MFS_ERR_NUMERIC). */
 mfs_status mfs_set_rigid_velocities(mfs_ctx* ctx, const double* v, const double* omega);
 mfs_status mfs_set_rigid_velocities_device(mfs_ctx* ctx, const double* d_v, const double* d_omega);
 
@@ -177,7 +179,8 @@ mfs_status mfs_set_forces_torques(mfs_ctx* ctx, const double* F, const double* T
 mfs_status mfs_get_rigid_velocities(mfs_ctx* ctx, double* v, double* omega);
 
 /* Background flow u_inf(x) = U + E x + Omega x x subtracted in eq. bc (Sec. 4, Ex. 2).
- * Each pointer may be NULL (term absent): U (3), E (3*3 row-major), Omega (3). */
+ * Each pointer may be NULL (term absent): U (3), E (3*3 row-major), Omega (3).  Non-finite
+ * values give MFS_ERR_ARG and leave the previous background flow in place. */
 mfs_status mfs_set_background_flow(mfs_ctx* ctx, const double* U, const double* E, const double* Omega);
 
 /* Discretise (contacts, image lines, caps, weights) and compute every distinct
@@ -250,8 +253,12 @@ mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat
  * allocated by mfs_build).  Its first call on a device looks up the array's device address;
  * make that first call before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other threads, contexts or streams) race and must be serialised by the
- * caller.  Nothing in the array needs clearing; each call overwrites what it reads.  Returns
- * after the context's stream has drained. */
+ * caller.  Nothing in the array needs clearing; each call overwrites what it reads.  The work
+ * runs on the context's stream, which is not ordered after the caller's other streams: d_mu
+ * must be complete when the call is made (synchronise the stream that wrote it first, or
+ * create the context on that stream with mfs_create).  The array's address is looked up again
+ * whenever the calling thread's CUDA context differs from the one of the previous lookup on
+ * that device (e.g. after cudaDeviceReset).  Returns after the context's stream has drained. */
 mfs_status mfs_apply_precond_noalloc(mfs_ctx* ctx, const double* d_mu, double* d_lambda_hat);
 
 /* ---- many independent problems ----
@@ -304,10 +311,35 @@ typedef struct {
   double by_kind_ms[3];
   long long by_kind_proxy[3];
   long long by_kind_image_nodes[3];
+  /* Gram-Schmidt kernels of the batched GMRES (dot products and updates against the Krylov
+   * basis, eq. resistance solved by GMRES): launches, summed device time, and the bytes they
+   * must move at the least: a dot product of j basis vectors with w over n active entries reads
+   * (j + 1) n doubles, an update w -= sum_i c_i V_i reads (j + 1) n and writes n doubles */
+  long long krylov_launches;
+  double krylov_ms;
+  double krylov_bytes;
 } mfs_timing_t;
 mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
 /* Copies the counters; reset != 0 zeroes them afterwards. */
 mfs_status mfs_get_timing(mfs_ctx* ctx, mfs_timing_t* out, int reset);
+
+/* Measured CUDA-core arithmetic peak of device `device`, the roofline denominator of the pair
+ * kernels (which are bound by FP32-pipe issue, not by a tensor-core contraction): a kernel of
+ * independent fused multiply-add chains, 8 per thread, on every SM, timed with CUDA events after
+ * a warm-up launch.  which = 0: FP32 FFMA; which = 1: FP64 DFMA.  *tflops receives
+ * 2 x FMAs / second / 1e12 (an FMA counts two flops) and *ms the timed launch's duration; the
+ * launch runs ~0.1-0.5 s.  Allocates and frees one small device buffer. */
+mfs_status mfs_probe_alu_peak(int device, int which, double* tflops, double* ms);
+
+/* Cap on the device memory the context may hold for its discretisation, factors and solver
+ * workspace (bytes; 0 = no cap, the default).  An allocation that would exceed it fails like a
+ * cudaMalloc failure: the call returns MFS_ERR_OOM and the context stays usable, so a caller
+ * that shares the GPU can keep this library inside its share.  The cap does not cover the
+ * transient scratch of the one-body SVDs inside mfs_build nor the workspace of the batched
+ * solves (which the first context of a batch holds). */
+mfs_status mfs_set_memory_limit(mfs_ctx* ctx, unsigned long long bytes);
+/* Device bytes the context currently holds under that accounting. */
+mfs_status mfs_memory_in_use(const mfs_ctx* ctx, unsigned long long* bytes);
 
 #ifdef __cplusplus
 }

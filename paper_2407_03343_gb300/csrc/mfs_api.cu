@@ -99,7 +99,7 @@ struct mfs_ctx {
   // measurement
   bool prof = false;
   mfs_timing_t tm{};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_krylov, ev_pool;
   std::vector<int> ev_pair_kind;  // precision of each pair launch in ev_pair
   long long pairs_per_apply = 0, proxy_per_apply = 0, image_per_apply = 0;
   long long build_id = 0;
@@ -112,8 +112,11 @@ struct mfs_ctx {
   HostDisc hd;
   cusolverDnHandle_t solver = nullptr;
 
-  // device memory owned by the current build
+  // device memory owned by the current build, with its size for the memory cap
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
+  unsigned long long mem_limit = 0;  // 0: no cap
+  unsigned long long mem_used = 0;
   TargetSet tg;
   SourceSet src;
   double* d_colloc_abs = nullptr;
@@ -144,16 +147,33 @@ struct mfs_ctx {
   T* dalloc(size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+    const size_t bytes = count * sizeof(T);
+    if (mem_limit && mem_used + bytes > mem_limit) return nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
     allocs.push_back(p);
+    alloc_bytes.push_back(bytes);
+    mem_used += bytes;
     return static_cast<T*>(p);
+  }
+  // frees one allocation made by dalloc
+  void dfree(void* p) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == p) {
+        cudaFree(p);
+        mem_used -= alloc_bytes[i];
+        allocs.erase(allocs.begin() + i);
+        alloc_bytes.erase(alloc_bytes.begin() + i);
+        return;
+      }
   }
   void free_build() {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
+    alloc_bytes.clear();
+    mem_used = 0;
     factors.clear();
     tg = TargetSet();
     src = SourceSet();
@@ -250,6 +270,12 @@ void collect_events(mfs_ctx* c) {
     c->ev_pool.push_back(e);
   }
   c->ev_gemv.clear();
+  for (auto& e : c->ev_krylov) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.krylov_ms += ms;
+    c->ev_pool.push_back(e);
+  }
+  c->ev_krylov.clear();
   cudaGetLastError();
 }
 
@@ -328,8 +354,7 @@ mfs_status ensure_krylov(mfs_ctx* c, int restart) {
   size_t need = (size_t)(restart + 1) * (size_t)c->n_sys * sizeof(T);
   if (c->basis_bytes < need) {
     if (c->d_basis) {
-      cudaFree(c->d_basis);
-      c->allocs.erase(std::remove(c->allocs.begin(), c->allocs.end(), c->d_basis), c->allocs.end());
+      c->dfree(c->d_basis);
       c->d_basis = nullptr;
     }
     c->d_basis = c->dalloc<char>(need);
@@ -841,6 +866,18 @@ void batch_apply_count(BatchRun& R, const std::vector<int>& act) {
     }
 }
 
+// Gram-Schmidt traffic of Arnoldi step j over the problems of `act`: two dot-product launches
+// against the j + 1 basis vectors (read (j + 1) n and w's n doubles each) and two updates
+// (read (j + 1) n, read and write w's n each), n the active problems' summed length
+void batch_krylov_count(BatchRun& R, const std::vector<int>& act, int j) {
+  BatchPlan* B = R.B;
+  long long n_act = 0;
+  for (int p = 0; p < B->K; ++p)
+    if (act[p]) n_act += B->voff[p + 1] - B->voff[p];
+  R.c0->tm.krylov_launches += 4;
+  R.c0->tm.krylov_bytes += 8.0 * (4.0 * j + 10.0) * (double)n_act;
+}
+
 void batch_apply(BatchRun& R, const double* in, double* out) {
   batch_apply_kernels(R, in, out);
   batch_apply_count(R, R.act);
@@ -854,7 +891,11 @@ mfs_status batch_norms(BatchRun& R, const double* v, std::vector<double>& nrm) {
   CUDA_TRY(R.c0, cudaMemcpyAsync(B->hpin, hn, sizeof(double) * B->K, cudaMemcpyDeviceToHost, R.st));
   CUDA_TRY(R.c0, cudaStreamSynchronize(R.st));
   nrm.assign(B->K, 0.0);
-  for (int p = 0; p < B->K; ++p) nrm[p] = R.act[p] ? std::sqrt(std::max(0.0, B->hpin[p])) : 0.0;
+  // a NaN stays NaN (std::max would turn it into 0 and hide non-finite data)
+  for (int p = 0; p < B->K; ++p) {
+    const double h = B->hpin[p];
+    nrm[p] = R.act[p] ? (std::isnan(h) ? h : std::sqrt(std::max(0.0, h))) : 0.0;
+  }
   return MFS_OK;
 }
 
@@ -967,15 +1008,18 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
   double* hn = B->hbuf + (size_t)2 * kMaxBatchVec * K;
   // the steps since the last synchronisation: flags after each step, for the work counters
   std::vector<int> window_start(act);
-  int in_window = 0, used = 0;
+  int in_window = 0, used = 0, last_j = -1;
   bool any = true;
   for (int j = 0; j < restart && used < iter_budget && any; ++j) {
+    last_j = j;
     double* w = V + (size_t)(j + 1) * n;
     batch_apply_kernels(R, V + (size_t)j * n, w);
-    launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h1, R.st);
-    launch_seg_update(B->seg, j + 1, V, n, h1, -1.0, w, R.st);
-    launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h2, R.st);
-    launch_seg_update(B->seg, j + 1, V, n, h2, -1.0, w, R.st);
+    timed(c, c->ev_krylov, [&] {
+      launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h1, R.st);
+      launch_seg_update(B->seg, j + 1, V, n, h1, -1.0, w, R.st);
+      launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h2, R.st);
+      launch_seg_update(B->seg, j + 1, V, n, h2, -1.0, w, R.st);
+    });
     launch_seg_dots(B->seg, 1, w, n, w, B->partial, hn, R.st);
     launch_batch_givens(S, j, h1, h2, hn, R.st);
     launch_seg_scale(B->seg, B->scl, w, w, R.st);
@@ -993,6 +1037,7 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
       std::vector<int> cur(window_start);
       for (int t = 0; t < in_window; ++t) {
         batch_apply_count(R, cur);
+        batch_krylov_count(R, cur, j - in_window + 1 + t);
         cur.assign(B->snap + (size_t)t * K, B->snap + (size_t)(t + 1) * K);
       }
       in_window = 0;
@@ -1010,6 +1055,7 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
     std::vector<int> cur(window_start);
     for (int t = 0; t < in_window; ++t) {
       batch_apply_count(R, cur);
+      batch_krylov_count(R, cur, last_j - in_window + 1 + t);
       cur.assign(B->snap + (size_t)t * K, B->snap + (size_t)(t + 1) * K);
     }
   }
@@ -1303,7 +1349,7 @@ void mfs_destroy(mfs_ctx* c) {
   delete c->batch;
   c->batch = nullptr;
   c->free_build();
-  for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_pool})
+  for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_krylov, &c->ev_pool})
     for (auto& e : *lst) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -1337,6 +1383,9 @@ mfs_status mfs_set_spheres(mfs_ctx* c, int P, const double* centres, const doubl
 
 mfs_status mfs_set_background_flow(mfs_ctx* c, const double* U, const double* E, const double* Om) {
   if (!c) return MFS_ERR_ARG;
+  for (int i = 0; i < 9; ++i)
+    if ((U && i < 3 && !std::isfinite(U[i])) || (E && !std::isfinite(E[i])) || (Om && i < 3 && !std::isfinite(Om[i])))
+      return c->fail(MFS_ERR_ARG, "non-finite background flow");
   std::fill(c->bg.begin(), c->bg.end(), 0.0);
   if (U) std::copy(U, U + 3, c->bg.begin());
   if (E) std::copy(E, E + 9, c->bg.begin() + 3);
@@ -1345,9 +1394,24 @@ mfs_status mfs_set_background_flow(mfs_ctx* c, const double* U, const double* E,
   return MFS_OK;
 }
 
+static mfs_status build_impl(mfs_ctx* c, const mfs_params* params);
+
 mfs_status mfs_build(mfs_ctx* c, const mfs_params* params) {
   mfs_status s = check_state(c, 1);
   if (s != MFS_OK) return s;
+  s = build_impl(c, params);
+  if (s != MFS_OK) {
+    // a failed build releases whatever it had allocated; the spheres stay set
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    c->free_build();
+    c->state = 1;
+  }
+  return s;
+}
+
+static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
+  mfs_status s = MFS_OK;
   mfs_params p;
   if (params) p = *params; else mfs_default_params(&p);
   c->free_build();
@@ -1807,6 +1871,8 @@ mfs_status mfs_set_rigid_velocities(mfs_ctx* c, const double* v, const double* o
   mfs_status s = check_state(c, 2);
   if (s != MFS_OK) return s;
   if (!v || !om) return c->fail(MFS_ERR_ARG, "null velocity array");
+  for (long long i = 0; i < 3LL * c->P; ++i)
+    if (!std::isfinite(v[i]) || !std::isfinite(om[i])) return c->fail(MFS_ERR_ARG, "non-finite rigid velocity");
   CUDA_TRY(c, cudaMemcpyAsync(c->d_v, v, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_om, om, sizeof(double) * 3 * c->P, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -2245,6 +2311,65 @@ mfs_status mfs_batch_solve_rhs_device(int n_problems, mfs_ctx* const* ctxs, cons
   return batch_rhs_common(n_problems, ctxs, d_v, d_omega, true, opts, infos, d_F, d_T);
 }
 
+mfs_status mfs_probe_alu_peak(int device, int which, double* tflops, double* ms) {
+  if ((which != 0 && which != 1) || !tflops) return MFS_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return MFS_ERR_CUDA;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return MFS_ERR_CUDA;
+  }
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, 16) != cudaSuccess) {
+    cudaGetLastError();
+    return MFS_ERR_OOM;
+  }
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mfs_status out = MFS_OK;
+  const int blocks = sms * 8;                   // 8 CTAs of 256 threads per SM
+  const int iters = which == 0 ? 40000 : 1200;  // ~0.2 s at the respective peak
+  float t = 0.f;
+  double flops = 0;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    out = MFS_ERR_CUDA;
+  } else {
+    launch_fma_probe(which, blocks, iters / 8, sink, st);  // warm-up
+    cudaEventRecord(e0, st);
+    flops = launch_fma_probe(which, blocks, iters, sink, st);
+    cudaEventRecord(e1, st);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess || !(t > 0.f))
+      out = MFS_ERR_CUDA;
+  }
+  cudaGetLastError();
+  if (out == MFS_OK) {
+    *tflops = flops / (t * 1e-3) / 1e12;
+    if (ms) *ms = t;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(sink);
+  return out;
+}
+
+mfs_status mfs_set_memory_limit(mfs_ctx* c, unsigned long long bytes) {
+  if (!c) return MFS_ERR_ARG;
+  c->mem_limit = bytes;
+  return MFS_OK;
+}
+
+mfs_status mfs_memory_in_use(const mfs_ctx* c, unsigned long long* bytes) {
+  if (!c || !bytes) return MFS_ERR_ARG;
+  *bytes = c->mem_used;
+  return MFS_OK;
+}
+
 mfs_status mfs_set_profiling(mfs_ctx* c, int on) {
   if (!c) return MFS_ERR_ARG;
   c->prof = on != 0;
@@ -2272,6 +2397,26 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 
 static std::mutex g_noalloc_mtx;
 static double* g_noalloc_ptr[64] = {nullptr};
+static void* g_noalloc_cuctx[64] = {nullptr};  // driver context of each cached lookup
+
+// The calling thread's current driver context (CUcontext), through the runtime's entry-point
+// query so that the library does not link the driver library itself; null if unavailable.
+static void* current_driver_context() {
+  using GetCurrent = int (*)(void**);
+  static GetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<GetCurrent>(f);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 mfs_status mfs_apply_precond_noalloc(mfs_ctx* c, const double* d_mu, double* d_lambda_hat) {
   mfs_status s = check_state(c, 2);  // also makes the context's device current
@@ -2284,9 +2429,11 @@ mfs_status mfs_apply_precond_noalloc(mfs_ctx* c, const double* d_mu, double* d_l
   if (c->device < 0 || c->device >= 64) return c->fail(MFS_ERR_ARG, "device index out of range for the static scratch table");
   double* scratch = nullptr;
   {
-    // first call on this device: resolve the array's device address with the device current
+    // first call on this device (or in a new driver context of it, e.g. after a device reset):
+    // resolve the array's device address with the device current
     std::lock_guard<std::mutex> g(g_noalloc_mtx);
-    if (!g_noalloc_ptr[c->device]) {
+    void* cu = current_driver_context();
+    if (!g_noalloc_ptr[c->device] || !cu || cu != g_noalloc_cuctx[c->device]) {
       double* ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
       if (e != cudaSuccess || !ptr) {
@@ -2294,6 +2441,7 @@ mfs_status mfs_apply_precond_noalloc(mfs_ctx* c, const double* d_mu, double* d_l
         return c->fail(MFS_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
       }
       g_noalloc_ptr[c->device] = ptr;
+      g_noalloc_cuctx[c->device] = cu;
     }
     scratch = g_noalloc_ptr[c->device];
   }

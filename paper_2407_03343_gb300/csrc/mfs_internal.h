@@ -214,6 +214,10 @@ void launch_batch_givens(const GivensState& S, int j, const double* h1, const do
 // coef[i K + p] = (R^{-1} g)_i over each problem's jused steps, zero up to jmax.
 void launch_batch_backsolve(const GivensState& S, int jmax, double* coef, cudaStream_t st);
 
+// Arithmetic-peak probe (which 0: FP32 FFMA, 1: FP64 DFMA) of `blocks` CTAs x 256 threads,
+// `iters` loop trips; returns the flops the launch performs.  sink: 8 writable bytes.
+double launch_fma_probe(int which, int blocks, int iters, void* sink, cudaStream_t st);
+
 // Forces and torques (Sec. 2.3 remark), FP64, one CTA per sphere.
 void launch_forces_torques(const SourceSet& src, const double* lam, double* F, double* T, cudaStream_t st);
 // the same with F, T written every `stride` doubles per sphere and scaled by sF, sT

@@ -1287,6 +1287,29 @@ __global__ void assemble_self_kernel(int m, int n_src, const double* __restrict_
     for (int rr = 0; rr < 3; ++rr) B[(3LL * s + c) * lda + 3LL * i + rr] = w * K[rr][c];
 }
 
+// Arithmetic-peak probe: 8 independent fused multiply-add chains per thread, 16 steps of each
+// per loop trip, enough warps per SM to hide the FMA latency.  The result is stored only when it
+// equals a value it never takes, so the chains cannot be removed.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T a, T b, T* __restrict__ sink) {
+  T x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = T(threadIdx.x + q) * T(1e-3);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if constexpr (sizeof(T) == 4) x[q] = __fmaf_rn(x[q], a, b);
+        else x[q] = __fma_rn(x[q], a, b);
+      }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  if (s == T(-1.25e30)) sink[0] = s;
+}
+
 thread_local long long t_launches = 0;
 
 inline int grid_for(long long n, int threads, int cap = 152 * 16) {
@@ -1511,6 +1534,13 @@ void launch_rhs(int n, const double* colloc_abs, const int* owner, const double*
   for (int i = 0; i < 15; ++i) b.v[i] = bg[i];
   ++t_launches;
   rhs_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, colloc_abs, owner, sqrtw, cen, v, om, b, wb);
+}
+
+double launch_fma_probe(int which, int blocks, int iters, void* sink, cudaStream_t st) {
+  ++t_launches;
+  if (which == 0) fma_probe_kernel<float><<<blocks, 256, 0, st>>>(iters, 0.9999f, 1e-4f, static_cast<float*>(sink));
+  else fma_probe_kernel<double><<<blocks, 256, 0, st>>>(iters, 0.9999, 1e-4, static_cast<double*>(sink));
+  return 2.0 * 8.0 * 16.0 * (double)iters * (double)blocks * 256.0;  // flops
 }
 
 void launch_assemble_self(const HostDisc& hd, int k, const double* d_colloc_rel, const double* d_sqrtw,

@@ -61,7 +61,8 @@ class Timing(C.Structure):
                 ("pair_image_nodes", C.c_longlong), ("pair_kind", C.c_int), ("gemv_launches", C.c_longlong),
                 ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double),
                 ("by_kind_launches", C.c_longlong * 3), ("by_kind_ms", C.c_double * 3),
-                ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3)]
+                ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3),
+                ("krylov_launches", C.c_longlong), ("krylov_ms", C.c_double), ("krylov_bytes", C.c_double)]
 
 
 class MfsError(RuntimeError):
@@ -116,6 +117,9 @@ def lib():
         "mfs_batch_solve_rhs_device": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                                  C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.POINTER(P), C.POINTER(P)]),
         "mfs_set_profiling": (C.c_int, [P, C.c_int]),
+        "mfs_probe_alu_peak": (C.c_int, [C.c_int, C.c_int, _D, _D]),
+        "mfs_set_memory_limit": (C.c_int, [P, C.c_ulonglong]),
+        "mfs_memory_in_use": (C.c_int, [P, C.POINTER(C.c_ulonglong)]),
         "mfs_get_timing": (C.c_int, [P, C.POINTER(Timing), C.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -345,6 +349,16 @@ class Context:
         self._check(self._L.mfs_get_timing(self._h, C.byref(t), 1 if reset else 0))
         return t
 
+    def set_memory_limit(self, nbytes: int):
+        """Cap the device memory this context may hold (0 = no cap); see mfs_set_memory_limit."""
+        self._check(self._L.mfs_set_memory_limit(self._h, int(nbytes)))
+
+    def memory_in_use(self) -> int:
+        """Device bytes the context holds under the cap's accounting."""
+        b = C.c_ulonglong(0)
+        self._check(self._L.mfs_memory_in_use(self._h, C.byref(b)))
+        return int(b.value)
+
     def apply_pairs(self, lam_hat, mu, precision=FP64):
         """mu + W sum over other spheres of G lambda_hat (steps 2 and 3)."""
         lam_hat = _f64(lam_hat)
@@ -352,6 +366,16 @@ class Context:
         out = np.zeros_like(mu)
         self._check(self._L.mfs_apply_pairs(self._h, int(precision), _dp(lam_hat), _dp(mu), _dp(out)))
         return out
+
+
+def probe_alu_peak(device: int = 0, kind: str = "fp32"):
+    """Measured FFMA (kind "fp32") or DFMA ("fp64") peak of the device: (TFLOP/s, ms of the launch)."""
+    t = C.c_double(0)
+    ms = C.c_double(0)
+    st = lib().mfs_probe_alu_peak(int(device), {"fp32": 0, "fp64": 1}[kind], C.byref(t), C.byref(ms))
+    if st != 0:
+        raise MfsError(st, "mfs_probe_alu_peak failed")
+    return t.value, ms.value
 
 
 def discretise_host(centres, radius=1.0, params: Params | None = None, **kw):

@@ -1,8 +1,11 @@
 """Parity at full sizes.
 
 * Gap-sweep problems at the benchmark's sizes (N = 800, R_p = 0.63, M0 = 1600, up to 20
-  image points per contact), solved as one lockstep batch in the mixed mode exactly as the
-  benchmark runs them, against the matrix-free FP64 oracle (O3).
+  image points per contact) with random rigid motions, solved as one lockstep batch in the
+  mixed mode at the tighter tolerance 1e-8 (so the refinement residual uses the native FP64
+  operator), against the matrix-free FP64 oracle (O3) solved on the fly.  The benchmarked
+  options themselves (tolerance 1e-6, double-float residual) are checked over all 54 sweep
+  problems in test_gpu_sweep_bench_config.py.
 * The 200-sphere suspension (volume fraction 0.2, ~300 near contacts, N = 800, M0 = 1600):
   its discretisation element by element, and the pair apply on sampled collocation rows that
   the oracle evaluates one by one (every FP64 / double-float / FP32 kernel, 4 nodes per thread).
