@@ -169,20 +169,21 @@ def oracle_sample(seconds_budget=20.0):
 
 def oracle_solve_sample():
     """One full oracle solve of a sweep problem (matrix-free GMRES on eq. resistance with the
-    three-step apply, O3) at the benchmark's tolerance, timed on the host: the delta = 0.0582
-    shear problem (images on both spheres).  Set-up (the two one-body SVDs) timed separately."""
+    three-step apply, O3) at the benchmark's tolerance, timed on the host: the hardest problem of
+    the sweep, squeezing at delta = 1e-3 (20 image points per sphere).  Set-up (the two one-body
+    SVDs) timed separately."""
     from oracle import geometry, solve
     from paper_2407_03343_gb300 import workloads
-    gap = workloads.gap_sweep_gaps()[9]
+    gap = workloads.gap_sweep_gaps()[0]
     t0 = time.perf_counter()
     d = geometry.build(workloads.two_spheres(gap), 1.0, geometry.Params(n_proxy=N_PROXY, r_proxy=R_PROXY,
                                                                         m_basic=M_BASIC))
     op = solve.Operator(d)
     t1 = time.perf_counter()
-    v, w = workloads.motion("shear")
+    v, w = workloads.motion("squeeze")
     sol = solve.solve_o3(d, v, w, op=op, tol=SWEEP_TOL)
     t2 = time.perf_counter()
-    return {"problem": f"gap {gap:.4g}, shear", "setup_s": t1 - t0, "solve_s": t2 - t1, "iters": sol.iters,
+    return {"problem": f"gap {gap:.4g}, squeeze", "setup_s": t1 - t0, "solve_s": t2 - t1, "iters": sol.iters,
             "cores": host_cores()}
 
 
