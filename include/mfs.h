@@ -65,6 +65,9 @@ typedef enum {
  *             converges only when B_k^+ amplifies by well under 1/eps_FP32, i.e. not with
  *             images and the paper's truncation 5e-12 (returns MFS_ERR_NOT_CONVERGED). */
 enum { MFS_FP64 = 0, MFS_MIXED = 1, MFS_FP32 = 2 };
+/* Single-step entry points only: the operator of the MFS_MIXED GMRES passes themselves (Sigma^+ U^T
+ * from its FP32 copy, and the far field when mfs_params.far_dist > 0). */
+enum { MFS_MIXED_PASS = 3 };
 
 /* Discretisation parameters (Sec. 2.1, Sec. 2.3, Sec. 5.1, App. A.1).
  * Defaults (mfs_default_params): the paper's coarse choice N = 686, R_p = 0.63,
@@ -91,6 +94,28 @@ typedef struct {
                            printed, eq. image_est).  Not in the paper: with nim_cut 0.3 and nim_min 2 the
                            gaps 0.15 <= delta < 0.3, where the printed rule places no images and the coarse
                            proxy sphere alone misses the 1e-3 target, get two images each */
+  /* Far field of the GMRES passes (not in the paper, which evaluates step 2 with an FMM): with
+   * far_dist > 0 a sphere k' whose centre is at least far_dist * a from the target sphere's acts in
+   * the MIXED passes through far_n_eq equivalent Stokeslets on radius far_r_eq * a about c_k',
+   * whose strengths are q_k' = Q mu_k' with Q = Pinv(S_ce) G_chk B_k'^+ formed once in FP64
+   * (S_ce: Stokeslets from the equivalent points to 2 far_n_eq check points on radius far_r_chk * a,
+   * pseudo-inverse truncated at far_eps of its largest singular value; G_chk: the sphere's own
+   * sources at the check points), so the amplification of B^+ never enters the FP32 sums.
+   * Nearer spheres are summed directly in double-float.  The refinement residual always uses
+   * every pair directly, so the far field changes how fast the passes run, not the accuracy of
+   * the solution.  Needs far_dist >= far_r_chk + 1.  Defaults: far_dist 0 (off), 300, 1.0, 2.0,
+   * 1e-6.  Single solves only; batched solves evaluate every pair directly. */
+  double far_dist;
+  int far_n_eq;
+  double far_r_eq;
+  double far_r_chk;
+  double far_eps;
+  /* Step 1 of the MIXED passes for the spheres without contacts, which share the basic factor
+   * (Sec. 2.2): 1 (default) as one matrix product on the tensor cores (tcgen05, bf16 slices with
+   * FP32 accumulation, the accuracy of the FP32 Sigma^+ U^T those passes use) once at least 8
+   * spheres share it, 2 whenever at least one does, 0 never (batched GEMV for every sphere).
+   * Applies to Sigma^+ U^T and, with the far field, to Q; single solves and single steps. */
+  int tensor_step1;
 } mfs_params;
 
 /* GMRES / refinement options (precision as above).  Every mode re-evaluates the residual
@@ -138,6 +163,8 @@ typedef struct {
   int n_factors;      /* distinct one-body factors (shared basic block + one per contact sphere) */
   long long pairs_fp; /* (target node, vector source) pairs of one operator apply, self blocks excluded;
                          an image S+R+D triple counts as 3 */
+  long long pairs_near_fp;  /* with the far field: of those, the pairs with near spheres (double-float) */
+  long long pairs_far_eq;   /* and the (target node, equivalent Stokeslet) pairs replacing the rest (FP32) */
 } mfs_sizes_t;
 
 void mfs_default_params(mfs_params* p);
@@ -318,6 +345,12 @@ typedef struct {
   long long krylov_launches;
   double krylov_ms;
   double krylov_bytes;
+  /* far field of the passes: launches of the FP32 equivalent-source kernel, their device time and
+   * the (target node, equivalent Stokeslet) pairs they evaluated; the near part of those applies
+   * is counted with the pair kernel above (pair_proxy / pair_image_nodes of the near spheres) */
+  long long far_launches;
+  double far_ms;
+  long long far_pairs;
 } mfs_timing_t;
 mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
 /* Copies the counters; reset != 0 zeroes them afterwards. */

@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include "mfs_internal.h"
@@ -43,6 +44,8 @@ struct Factor {
   float* V32 = nullptr;
   float2* A2 = nullptr;   // (hi, lo) float pairs of A64 and V64 for the double-float GEMV
   float2* V2 = nullptr;
+  float* Q32 = nullptr;   // far field: 3 n_eq x ldQ (row-major), collocation data -> equivalent strengths
+  int ldQ = 0;
 };
 
 // keep[i] is the SVD column index of the i-th retained singular triplet
@@ -90,6 +93,7 @@ struct mfs_ctx {
   bool solved = false;
   bool dw_pairs = false;  // FP64 operator uses the double-float pair kernel and factors
   bool dw_fast_a = false; // with dw_pairs: Sigma^+ U^T read from its FP32 copy (inner MIXED solves)
+  bool ff_pass = false;   // with dw_pairs: far spheres through their equivalent sources (inner MIXED solves)
   bool factored = false;  // one-body pseudo-inverses available
   int mode = 0;           // 0: resistance (velocities given), 1: mobility (forces/torques given)
   int n_sys = 0;          // GMRES system size: n, or n + 6P for the bordered mobility system
@@ -99,9 +103,11 @@ struct mfs_ctx {
   // measurement
   bool prof = false;
   mfs_timing_t tm{};
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_krylov, ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pair, ev_gemv, ev_krylov, ev_far, ev_pool;
   std::vector<int> ev_pair_kind;  // precision of each pair launch in ev_pair
   long long pairs_per_apply = 0, proxy_per_apply = 0, image_per_apply = 0;
+  // with the far field: near pairs of one apply and the equivalent-source pairs replacing the rest
+  long long near_pairs_per_apply = 0, near_proxy_per_apply = 0, near_image_per_apply = 0, far_pairs_per_apply = 0;
   long long build_id = 0;
   struct BatchPlan* batch = nullptr;  // cached lockstep-batch workspace (owned when this is the first context)
   double gemv_bytes32 = 0, gemv_bytes64 = 0, gemv_bytes_fast = 0;  // factor bytes per step 1
@@ -123,6 +129,16 @@ struct mfs_ctx {
   int* d_owner = nullptr;
   double* d_sqrtw = nullptr;
   std::vector<Factor> factors;
+  FarField ff;             // n_eq == 0: no far field
+  float* d_q = nullptr;    // equivalent strengths, 3 n_eq per sphere
+  GemvBatch<float> gQ;     // q = Q_f mu_k for every sphere
+  // tensor-core step 1 of the passes for the spheres that share the basic factor
+  int tc_ncols = 0;        // such spheres on the tensor path (0: off)
+  TcGemm tcA, tcQ;         // Sigma^+ U^T and Q of the shared factor, bf16 slices
+  long long *d_tc_xoff = nullptr, *d_tc_yA = nullptr, *d_tc_yQ = nullptr;
+  float* d_tc_partial = nullptr;
+  int* d_tc_err = nullptr;
+  GemvBatch<float> gA32_rest, gQ_rest;  // the GEMV jobs of every other sphere
   GemvBatch<float> gA32, gV32;
   GemvBatch<double> gA64, gV64;
   long long tmp_len = 0;
@@ -175,6 +191,13 @@ struct mfs_ctx {
     alloc_bytes.clear();
     mem_used = 0;
     factors.clear();
+    ff = FarField();
+    d_q = nullptr;
+    gQ = GemvBatch<float>();
+    tc_ncols = 0;
+    tcA = TcGemm();
+    tcQ = TcGemm();
+    gA32_rest = gQ_rest = GemvBatch<float>();
     tg = TargetSet();
     src = SourceSet();
     d_basis = nullptr;
@@ -276,6 +299,12 @@ void collect_events(mfs_ctx* c) {
     c->ev_pool.push_back(e);
   }
   c->ev_krylov.clear();
+  for (auto& e : c->ev_far) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) c->tm.far_ms += ms;
+    c->ev_pool.push_back(e);
+  }
+  c->ev_far.clear();
   cudaGetLastError();
 }
 
@@ -287,8 +316,16 @@ void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
     if constexpr (sizeof(T) == 8) {
       if (c->dw_pairs) {
         launch_split_dw(c->n, mu, c->d_x2, c->stream);
-        if (c->dw_fast_a) launch_gemv_f32_dw(c->gA32, c->d_x2, c->d_t2, c->stream);
-        else launch_gemv_dw(Ops<T>::A(c), c->d_x2, c->d_t2, nullptr, c->stream);
+        if (c->dw_fast_a && c->tc_ncols > 0) {
+          // the spheres sharing the basic factor as one product on the tensor cores
+          launch_gemv_f32_dw(c->gA32_rest, c->d_x2, c->d_t2, c->stream);
+          launch_tc_gemm(c->tcA, c->tc_ncols, mu, c->d_tc_xoff, c->d_tc_yA, nullptr, c->d_t2, c->d_tc_partial,
+                         c->d_tc_err, true, c->stream);
+        } else if (c->dw_fast_a) {
+          launch_gemv_f32_dw(c->gA32, c->d_x2, c->d_t2, c->stream);
+        } else {
+          launch_gemv_dw(Ops<T>::A(c), c->d_x2, c->d_t2, nullptr, c->stream);
+        }
         launch_gemv_dw(Ops<T>::V(c), c->d_t2, nullptr, lam_hat, c->stream);
         return;
       }
@@ -304,6 +341,38 @@ void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
 // steps 2+3 with the pair kernel of the current precision
 template <typename T>
 void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
+  if constexpr (sizeof(T) == 8) {
+    if (c->dw_pairs && c->ff_pass && c->ff.n_eq > 0) {
+      // near spheres directly in double-float, the far ones through their equivalent sources,
+      // whose strengths q = Q mu are formed from this apply's mu
+      timed(c, c->ev_pair, [&] {
+        launch_pairs_dw_near(c->tg, c->src, c->ff, lam_hat, mu, out, c->hd.prm.visc, c->stream);
+      });
+      timed(c, c->ev_far, [&] {
+        launch_convert<double, float>(c->n, mu, 1.0, c->d_mu32, c->stream);
+        if (c->tc_ncols > 0) {
+          launch_gemv<float>(c->gQ_rest, c->d_mu32, c->d_q, c->stream);
+          launch_tc_gemm(c->tcQ, c->tc_ncols, mu, c->d_tc_xoff, c->d_tc_yQ, c->d_q, nullptr, c->d_tc_partial,
+                         c->d_tc_err, true, c->stream);
+        } else {
+          launch_gemv<float>(c->gQ, c->d_mu32, c->d_q, c->stream);
+        }
+        launch_pairs_far(c->tg, c->src, c->ff, out, c->hd.prm.visc, c->stream);
+      });
+      c->tm.pair_launches += 1;
+      c->tm.pair_interactions += c->near_pairs_per_apply;
+      c->tm.pair_proxy += c->near_proxy_per_apply;
+      c->tm.pair_image_nodes += c->near_image_per_apply;
+      c->tm.pair_kind = MFS_MIXED;
+      c->tm.by_kind_launches[MFS_MIXED] += 1;
+      c->tm.by_kind_proxy[MFS_MIXED] += c->near_proxy_per_apply;
+      c->tm.by_kind_image_nodes[MFS_MIXED] += c->near_image_per_apply;
+      c->tm.far_launches += 1;
+      c->tm.far_pairs += c->far_pairs_per_apply;
+      if (c->prof) c->ev_pair_kind.push_back(MFS_MIXED);
+      return;
+    }
+  }
   timed(c, c->ev_pair, [&] {
     if constexpr (sizeof(T) == 8) {
       if (c->dw_pairs) {
@@ -492,6 +561,17 @@ mfs_status norm64(mfs_ctx* c, const double* v, double& out) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   out = std::sqrt(r2);
   return MFS_OK;
+}
+
+// A bounded wait of the tensor-core kernel ran out (its flag is cleared for the next call).
+mfs_status check_tc_timeout(mfs_ctx* c) {
+  if (!c->d_tc_err) return MFS_OK;
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (!h) return MFS_OK;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream));
+  return c->fail(MFS_ERR_TIMEOUT, "tensor-core step 1: a pipeline wait ran out of time");
 }
 
 mfs_status check_state(mfs_ctx* c, int need) {
@@ -1303,6 +1383,12 @@ void mfs_default_params(mfs_params* p) {
   p->visc = 1.0;
   p->build_factors = 1;
   p->nim_min = 0;
+  p->far_dist = 0.0;
+  p->far_n_eq = 300;
+  p->far_r_eq = 1.0;
+  p->far_r_chk = 2.0;
+  p->far_eps = 1e-6;
+  p->tensor_step1 = 1;
 }
 
 void mfs_default_solve_opts(mfs_solve_opts* o) {
@@ -1349,7 +1435,7 @@ void mfs_destroy(mfs_ctx* c) {
   delete c->batch;
   c->batch = nullptr;
   c->free_build();
-  for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_krylov, &c->ev_pool})
+  for (auto* lst : {&c->ev_pair, &c->ev_gemv, &c->ev_krylov, &c->ev_far, &c->ev_pool})
     for (auto& e : *lst) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -1515,6 +1601,95 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     max_nc = std::max(max_nc, ncol);
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // geometry uploads done before workers start
+
+  // ---- far field, the part every sphere shares: the pseudo-inverse of the Stokeslet block from
+  // the equivalent points to the check points, truncated at far_eps of its largest singular value
+  const bool far_on = p.far_dist > 0 && nf > 0;
+  const int n_eq = far_on ? p.far_n_eq : 0, n_chk = 2 * n_eq;
+  std::vector<void*> far_tmp;  // build-time buffers of the far field, freed at the end of the build
+  struct FarTmpFree {
+    std::vector<void*>& v;
+    ~FarTmpFree() {
+      for (void* q : v) cudaFree(q);
+    }
+  } far_tmp_free{far_tmp};
+  auto far_alloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    far_tmp.push_back(q);
+    return q;
+  };
+  double *d_pinv = nullptr, *d_chk = nullptr, *d_ones = nullptr;
+  std::vector<double> eq_host;
+  if (far_on) {
+    std::vector<double> chk, ones(n_chk, 1.0);
+    std::vector<int> ty0(n_eq, 0);
+    fibonacci_sphere(n_eq, p.far_r_eq * c->a, eq_host);
+    fibonacci_sphere(n_chk, p.far_r_chk * c->a, chk);
+    const int me = 3 * n_chk, ne = 3 * n_eq;
+    d_chk = (double*)far_alloc(sizeof(double) * chk.size());
+    d_ones = (double*)far_alloc(sizeof(double) * n_chk);
+    double* d_eq = (double*)far_alloc(sizeof(double) * eq_host.size());
+    int* d_ty0 = (int*)far_alloc(sizeof(int) * n_eq);
+    double* d_S = (double*)far_alloc(sizeof(double) * (size_t)me * ne);
+    double* d_U = (double*)far_alloc(sizeof(double) * (size_t)me * ne);
+    double* d_VT = (double*)far_alloc(sizeof(double) * (size_t)ne * ne);
+    double* d_s = (double*)far_alloc(sizeof(double) * ne);
+    double* d_sinv = (double*)far_alloc(sizeof(double) * ne);
+    double* d_rw = (double*)far_alloc(sizeof(double) * ne);
+    int* d_info = (int*)far_alloc(sizeof(int));
+    d_pinv = (double*)far_alloc(sizeof(double) * (size_t)ne * me);
+    if (!d_chk || !d_ones || !d_eq || !d_ty0 || !d_S || !d_U || !d_VT || !d_s || !d_sinv || !d_rw || !d_info || !d_pinv)
+      return c->fail(MFS_ERR_OOM, "device allocation failed: far-field fit");
+    CUDA_TRY(c, cudaMemcpyAsync(d_chk, chk.data(), sizeof(double) * chk.size(), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(d_ones, ones.data(), sizeof(double) * n_chk, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(d_eq, eq_host.data(), sizeof(double) * eq_host.size(), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(d_ty0, ty0.data(), sizeof(int) * n_eq, cudaMemcpyHostToDevice, c->stream));
+    launch_assemble_block(n_chk, n_eq, d_chk, d_ones, d_eq, d_ty0, p.visc, d_S, me, c->stream);
+    CHECK_LAUNCH(c);
+    cusolverDnHandle_t hs = nullptr;
+    cublasHandle_t hb = nullptr;
+    struct Handles {
+      cusolverDnHandle_t& s;
+      cublasHandle_t& b;
+      ~Handles() {
+        if (s) cusolverDnDestroy(s);
+        if (b) cublasDestroy(b);
+      }
+    } handles{hs, hb};
+    if (cusolverDnCreate(&hs) != CUSOLVER_STATUS_SUCCESS || cusolverDnSetStream(hs, c->stream) != CUSOLVER_STATUS_SUCCESS ||
+        cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS || cublasSetStream(hb, c->stream) != CUBLAS_STATUS_SUCCESS)
+      return c->fail(MFS_ERR_CUDA, "far field: cuSOLVER / cuBLAS handle creation failed");
+    int lw = 0;
+    CUSOLVER_TRY(c, cusolverDnDgesvd_bufferSize(hs, me, ne, &lw));
+    double* d_work = (double*)far_alloc(sizeof(double) * (size_t)std::max(lw, 1));
+    if (!d_work) return c->fail(MFS_ERR_OOM, "device allocation failed: far-field SVD workspace");
+    CUSOLVER_TRY(c, cusolverDnDgesvd(hs, 'S', 'S', me, ne, d_S, me, d_s, d_U, me, d_VT, ne, d_work, lw, d_rw, d_info));
+    std::vector<double> hsv(ne);
+    int hinfo = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(hsv.data(), d_s, sizeof(double) * ne, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(&hinfo, d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (hinfo != 0) return c->fail(MFS_ERR_CUDA, "far field: SVD of the equivalent-source block failed");
+    double smax = 0;
+    for (double v : hsv) smax = std::max(smax, v);
+    std::vector<double> sinv(ne, 0.0);
+    for (int i = 0; i < ne; ++i)
+      if (hsv[i] >= p.far_eps * smax && hsv[i] > 0) sinv[i] = 1.0 / hsv[i];
+    CUDA_TRY(c, cudaMemcpyAsync(d_sinv, sinv.data(), sizeof(double) * ne, cudaMemcpyHostToDevice, c->stream));
+    // Pinv = V diag(sinv) U^T: scale the columns of U, then (VT)^T (U diag(sinv))^T
+    // (d_S, overwritten by the SVD, receives U diag(sinv))
+    if (cublasDdgmm(hb, CUBLAS_SIDE_RIGHT, me, ne, d_U, me, d_sinv, 1, d_S, me) != CUBLAS_STATUS_SUCCESS)
+      return c->fail(MFS_ERR_CUDA, "far field: cublasDdgmm failed");
+    const double one = 1.0, zero = 0.0;
+    if (cublasDgemm(hb, CUBLAS_OP_T, CUBLAS_OP_T, ne, me, ne, &one, d_VT, ne, d_S, me, &zero, d_pinv, ne) !=
+        CUBLAS_STATUS_SUCCESS)
+      return c->fail(MFS_ERR_CUDA, "far field: cublasDgemm (pseudo-inverse) failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
   c->factors.assign(nf, Factor());
   const int n_workers = std::max(0, std::min(nf, 8));
   std::mutex mtx;
@@ -1531,6 +1706,7 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     if (cudaSetDevice(c->device) != cudaSuccess) return fail_w(MFS_ERR_CUDA, "cudaSetDevice in factor worker");
     cudaStream_t st = nullptr;
     cusolverDnHandle_t h = nullptr;
+    cublasHandle_t hb = nullptr;
     std::vector<void*> scratch;
     auto salloc = [&](size_t bytes) -> void* {
       void* q = nullptr;
@@ -1545,10 +1721,12 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
       if (st) cudaStreamSynchronize(st);
       for (void* q : scratch) cudaFree(q);
       if (h) cusolverDnDestroy(h);
+      if (hb) cublasDestroy(hb);
       if (st) cudaStreamDestroy(st);
     };
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS ||
-        cusolverDnSetStream(h, st) != CUSOLVER_STATUS_SUCCESS) {
+        cusolverDnSetStream(h, st) != CUSOLVER_STATUS_SUCCESS ||
+        (far_on && (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS || cublasSetStream(hb, st) != CUBLAS_STATUS_SUCCESS))) {
       cudaGetLastError();
       cleanup();
       return fail_w(MFS_ERR_CUDA, "factor worker: stream or cuSOLVER handle creation failed");
@@ -1573,6 +1751,19 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     if (!dB || !dU || !dVT || !dS || !drw || !dwork || !dinfo || !dxr || !dsw || !dyr || !dty || !dkeep) {
       cleanup();
       return fail_w(MFS_ERR_OOM, "device allocation failed: factorisation scratch");
+    }
+    // far field: the check-point field of the sphere's sources, its products with V and
+    // Sigma^+ U^T, and Q in FP64 before rounding
+    double *dG = nullptr, *dT1 = nullptr, *dT2 = nullptr, *dQ64 = nullptr;
+    if (far_on) {
+      dG = (double*)salloc(sizeof(double) * 3 * (size_t)n_chk * max_nc);
+      dT1 = (double*)salloc(sizeof(double) * 3 * (size_t)n_chk * max_nc);
+      dT2 = (double*)salloc(sizeof(double) * 3 * (size_t)n_chk * max_m);
+      dQ64 = (double*)salloc(sizeof(double) * (size_t)pad4(max_m) * 3 * n_eq);
+      if (!dG || !dT1 || !dT2 || !dQ64) {
+        cleanup();
+        return fail_w(MFS_ERR_OOM, "device allocation failed: far-field scratch");
+      }
     }
     std::vector<double> hS(max_nc);
     for (int f = wid; f < nf; f += n_workers) {
@@ -1665,6 +1856,34 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
       }
       pack_A_kernel<<<1024, 256, 0, st>>>(r, m, F.ldA, dU, dS, dkeep, F.A64, F.A32, F.A2);
       pack_V_kernel<<<1024, 256, 0, st>>>(ncol, r, F.ldV, dVT, dkeep, F.V64, F.V32, F.V2);
+      if (far_on) {
+        // Q = Pinv (G_chk (V (Sigma^+ U^T))): the check-point field of B^+ first, in FP64, so the
+        // amplified directions of B^+ only ever meet fields that are correspondingly weak
+        F.ldQ = pad4(m);
+        {
+          std::lock_guard<std::mutex> g(mtx);
+          F.Q32 = c->dalloc<float>((size_t)3 * n_eq * F.ldQ);
+        }
+        if (!F.Q32) {
+          fail_w(MFS_ERR_OOM, "device allocation failed: far-field matrices");
+          break;
+        }
+        const int mc = 3 * n_chk, ne = 3 * n_eq;
+        const double one = 1.0, zero = 0.0;
+        launch_assemble_block(n_chk, n_src, d_chk, d_ones, dyr, dty, p.visc, dG, mc, st);
+        cudaMemsetAsync(dQ64, 0, sizeof(double) * (size_t)F.ldQ * ne, st);
+        bool okb = cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, mc, r, ncol, &one, dG, mc, F.V64, F.ldV, &zero, dT1, mc) ==
+                       CUBLAS_STATUS_SUCCESS &&
+                   cublasDgemm(hb, CUBLAS_OP_N, CUBLAS_OP_T, mc, m, r, &one, dT1, mc, F.A64, F.ldA, &zero, dT2, mc) ==
+                       CUBLAS_STATUS_SUCCESS &&
+                   cublasDgemm(hb, CUBLAS_OP_T, CUBLAS_OP_T, m, ne, mc, &one, dT2, mc, d_pinv, ne, &zero, dQ64,
+                               F.ldQ) == CUBLAS_STATUS_SUCCESS;
+        if (!okb) {
+          fail_w(MFS_ERR_CUDA, "far field: cublasDgemm (Q) failed");
+          break;
+        }
+        launch_convert<double, float>((long long)F.ldQ * ne, dQ64, 1.0, F.Q32, st);
+      }
       cudaError_t el = cudaGetLastError();
       if (el == cudaSuccess) el = cudaStreamSynchronize(st);  // keep and hS are reused next round
       if (el != cudaSuccess) {
@@ -1681,6 +1900,79 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     for (auto& t : pool) t.join();
   }
   if (wstat != MFS_OK) return c->fail(wstat, werr);
+
+  // ---- far field: neighbour lists, equivalent points, the per-sphere Q GEMV
+  if (far_on) {
+    FarField& ff = c->ff;
+    ff.n_eq = n_eq;
+    std::vector<float4> e32(n_eq);
+    for (int e = 0; e < n_eq; ++e)
+      e32[e] = make_float4((float)eq_host[3 * e], (float)eq_host[3 * e + 1], (float)eq_host[3 * e + 2], 0.f);
+    std::vector<int> noff(1, 0), nidx, xoff(1, 0), xidx;
+    const double fd2 = (p.far_dist * c->a) * (p.far_dist * c->a);
+    long long np = 0, ni = 0, nfar = 0;
+    for (int k = 0; k < P; ++k) {
+      const long long mk = d.colloc_off[k + 1] - d.colloc_off[k];
+      int n_near = 0;
+      for (int k2 = 0; k2 < P; ++k2) {
+        if (k2 == k) {
+          xidx.push_back(k);
+          continue;
+        }
+        double r2 = 0;
+        for (int q = 0; q < 3; ++q) {
+          const double dq = d.centres[3 * k + q] - d.centres[3 * k2 + q];
+          r2 += dq * dq;
+        }
+        if (r2 < fd2) {
+          nidx.push_back(k2);
+          xidx.push_back(k2);
+          ++n_near;
+          np += mk * N;
+          ni += mk * (d.img_off[k2 + 1] - d.img_off[k2]);
+        }
+      }
+      noff.push_back((int)nidx.size());
+      xoff.push_back((int)xidx.size());
+      nfar += mk * (long long)n_eq * (P - 1 - n_near);
+    }
+    if (nidx.empty()) nidx.push_back(0);
+    if ((s = upload(c, ff.eq32, e32)) != MFS_OK || (s = upload(c, ff.near_off, noff)) != MFS_OK ||
+        (s = upload(c, ff.near_idx, nidx)) != MFS_OK || (s = upload(c, ff.excl_off, xoff)) != MFS_OK ||
+        (s = upload(c, ff.excl_idx, xidx)) != MFS_OK)
+      return s;
+    ALLOC_TRY(c, c->d_q, float, 3 * (size_t)n_eq * P);
+    ff.q = c->d_q;
+    c->near_proxy_per_apply = np;
+    c->near_image_per_apply = ni;
+    c->near_pairs_per_apply = np + 3 * ni;
+    c->far_pairs_per_apply = nfar;
+    std::vector<const float*> mQ(P);
+    std::vector<int> rQ(P, 3 * n_eq), cQ(P), lQ(P);
+    std::vector<long long> xQ(P), yQ(P);
+    for (int k = 0; k < P; ++k) {
+      const Factor& F = c->factors[d.factor_id[k]];
+      mQ[k] = F.Q32;
+      cQ[k] = F.m;
+      lQ[k] = F.ldQ;
+      xQ[k] = 3LL * d.colloc_off[k];
+      yQ[k] = 3LL * n_eq * k;
+    }
+    const float** dmQ = nullptr;
+    int *drQ, *dcQ, *dlQ;
+    long long *dxQ, *dyQ;
+    if ((s = upload(c, dmQ, mQ)) || (s = upload(c, drQ, rQ)) || (s = upload(c, dcQ, cQ)) || (s = upload(c, dlQ, lQ)) ||
+        (s = upload(c, dxQ, xQ)) || (s = upload(c, dyQ, yQ)))
+      return s;
+    c->gQ.mat = dmQ;
+    c->gQ.rows = drQ;
+    c->gQ.cols = dcQ;
+    c->gQ.ld = dlQ;
+    c->gQ.x_off = dxQ;
+    c->gQ.y_off = dyQ;
+    c->gQ.n_jobs = P;
+    c->gQ.max_rows = 3 * n_eq;
+  }
 
   // ---- GEMV batches for step 1
   std::vector<long long> tmp_off(P + 1, 0);
@@ -1740,6 +2032,100 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     c->gV64.y_off = c->gV32.y_off = d_yV;
     c->gV64.n_jobs = c->gV32.n_jobs = P;
     c->gV64.max_rows = c->gV32.max_rows = maxV;
+  }
+
+  // ---- tensor-core step 1: the spheres without contacts share the basic factor; their
+  // Sigma^+ U^T (and far-field Q) products in the passes become one matrix product each
+  {
+    int shared_f = -1;
+    for (int k = 0; k < P && nf > 0; ++k)
+      if (d.img_off[k + 1] == d.img_off[k] && d.colloc_off[k + 1] - d.colloc_off[k] == p.m_basic) {
+        shared_f = d.factor_id[k];
+        break;
+      }
+    std::vector<int> tck, rest;
+    for (int k = 0; k < P; ++k) {
+      if (shared_f >= 0 && d.factor_id[k] == shared_f) tck.push_back(k);
+      else rest.push_back(k);
+    }
+    const int tc_min = p.tensor_step1 == 2 ? 1 : 8;
+    if (nf > 0 && p.tensor_step1 != 0 && (int)tck.size() >= tc_min) {
+      const Factor& F = c->factors[shared_f];
+      const int ldk = tc_ldk(F.m), ncap = (int)tck.size();
+      void* as[3];
+      void* xs[3];
+      for (int i = 0; i < 3; ++i) {
+        as[i] = c->dalloc<uint16_t>((size_t)F.rank * ldk);
+        xs[i] = c->dalloc<uint16_t>((size_t)ncap * ldk);
+        if (!as[i] || !xs[i]) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
+      }
+      launch_split3_matrix(F.rank, F.m, F.ldA, F.A64, ldk, as[0], as[1], as[2], c->stream);
+      if (!tc_prepare(c->tcA, as, F.rank, xs, ncap, F.m))
+        return c->fail(MFS_ERR_CUDA, "tensor-core step 1: tensor maps or shared-memory limit unavailable");
+      size_t part = tc_partial_floats(c->tcA, ncap);
+      std::vector<long long> xo(ncap), ya(ncap), yq(ncap);
+      for (int i = 0; i < ncap; ++i) {
+        const int k = tck[i];
+        xo[i] = 3LL * d.colloc_off[k];
+        ya[i] = tmp_off[k];
+        yq[i] = 3LL * n_eq * k;
+      }
+      if (far_on) {
+        void* qs[3];
+        for (int i = 0; i < 3; ++i) {
+          qs[i] = c->dalloc<uint16_t>((size_t)3 * n_eq * ldk);
+          if (!qs[i]) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
+        }
+        launch_split3_matrix_f32(3 * n_eq, F.m, F.ldQ, F.Q32, ldk, qs[0], qs[1], qs[2], c->stream);
+        if (!tc_prepare(c->tcQ, qs, 3 * n_eq, xs, ncap, F.m))
+          return c->fail(MFS_ERR_CUDA, "tensor-core step 1: tensor maps unavailable");
+        part = std::max(part, tc_partial_floats(c->tcQ, ncap));
+        if ((s = upload(c, c->d_tc_yQ, yq)) != MFS_OK) return s;
+      }
+      if ((s = upload(c, c->d_tc_xoff, xo)) != MFS_OK || (s = upload(c, c->d_tc_yA, ya)) != MFS_OK) return s;
+      ALLOC_TRY(c, c->d_tc_partial, float, part);
+      ALLOC_TRY(c, c->d_tc_err, int, 1);
+      CUDA_TRY(c, cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream));
+      CHECK_LAUNCH(c);
+      // GEMV jobs of the other spheres
+      auto sub_batch = [&](GemvBatch<float>& out, bool q) -> mfs_status {
+        std::vector<const float*> mm;
+        std::vector<int> rr, cc, ll;
+        std::vector<long long> xx, yy;
+        int mx = 0;
+        for (int k : rest) {
+          const Factor& G = c->factors[d.factor_id[k]];
+          mm.push_back(q ? G.Q32 : G.A32);
+          rr.push_back(q ? 3 * n_eq : G.rank);
+          cc.push_back(G.m);
+          ll.push_back(q ? G.ldQ : G.ldA);
+          xx.push_back(3LL * d.colloc_off[k]);
+          yy.push_back(q ? 3LL * n_eq * k : tmp_off[k]);
+          mx = std::max(mx, rr.back());
+        }
+        out = GemvBatch<float>();
+        out.n_jobs = (int)mm.size();
+        out.max_rows = mx;
+        if (mm.empty()) return MFS_OK;
+        const float** dm = nullptr;
+        int *dr, *dc, *dl;
+        long long *dx, *dy;
+        mfs_status st2;
+        if ((st2 = upload(c, dm, mm)) || (st2 = upload(c, dr, rr)) || (st2 = upload(c, dc, cc)) ||
+            (st2 = upload(c, dl, ll)) || (st2 = upload(c, dx, xx)) || (st2 = upload(c, dy, yy)))
+          return st2;
+        out.mat = dm;
+        out.rows = dr;
+        out.cols = dc;
+        out.ld = dl;
+        out.x_off = dx;
+        out.y_off = dy;
+        return MFS_OK;
+      };
+      if ((s = sub_batch(c->gA32_rest, false)) != MFS_OK) return s;
+      if (far_on && (s = sub_batch(c->gQ_rest, true)) != MFS_OK) return s;
+      c->tc_ncols = ncap;
+    }
   }
 
   // ---- work vectors
@@ -1864,6 +2250,8 @@ mfs_status mfs_sizes(const mfs_ctx* cc, mfs_sizes_t* out) {
     pairs += mk * other;
   }
   out->pairs_fp = pairs;
+  out->pairs_near_fp = c->ff.n_eq > 0 ? c->near_pairs_per_apply : pairs;
+  out->pairs_far_eq = c->ff.n_eq > 0 ? c->far_pairs_per_apply : 0;
   return MFS_OK;
 }
 
@@ -1981,6 +2369,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
     // equation solved again if a restart-limited pass fell short (iterative refinement).
     c->dw_pairs = (o.precision == MFS_MIXED);
     c->dw_fast_a = c->dw_pairs;
+    c->ff_pass = c->dw_pairs;  // far field (if built) in the passes only
     CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * n, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_r, c->d_wb, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
     double rn = bnorm;
@@ -1993,7 +2382,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
       // solve G_hat e = r with the relative accuracy still missing, then mu += e
       if ((s = gmres<double>(c, c->d_r, c->d_w64, std::min(0.5, 0.5 * o.tol / rel), o.restart, o.max_iter - iters,
                              it_in, est)) != MFS_OK) {
-        c->dw_pairs = c->dw_fast_a = false;
+        c->dw_pairs = c->dw_fast_a = c->ff_pass = false;
         return s;
       }
       iters += it_in;
@@ -2006,26 +2395,26 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
       // have to contract the error, and the final accuracy is that of FP64), or, at tolerances
       // far above its accuracy floor, with the double-float operator
       c->dw_pairs = dw_residual(o);
-      c->dw_fast_a = false;
+      c->dw_fast_a = c->ff_pass = false;
       sys_apply<double>(c, c->d_mu, c->d_w64);
       c->dw_pairs = (o.precision == MFS_MIXED);
-      c->dw_fast_a = c->dw_pairs;
+      c->dw_fast_a = c->ff_pass = c->dw_pairs;
       launch_sub(n, c->d_wb, c->d_w64, c->d_r, c->stream);
       CHECK_LAUNCH(c);
       double rprev = rn;
       if ((s = norm64(c, c->d_r, rn)) != MFS_OK) {
-        c->dw_pairs = c->dw_fast_a = false;
+        c->dw_pairs = c->dw_fast_a = c->ff_pass = false;
         return s;
       }
       rel = rn / bnorm;
       if (it > 0) ++refinements;
       if (!std::isfinite(rn)) {
-        c->dw_pairs = c->dw_fast_a = false;
+        c->dw_pairs = c->dw_fast_a = c->ff_pass = false;
         return c->fail(MFS_ERR_NUMERIC, "residual is not finite");
       }
       if (rn > 0.9 * rprev && rel > o.tol) break;
     }
-    c->dw_pairs = c->dw_fast_a = false;
+    c->dw_pairs = c->dw_fast_a = c->ff_pass = false;
     converged = rel <= o.tol;
   } else {
     // MFS_FP32: FP64 residual, FP32 inner GMRES on the normalised residual
@@ -2073,6 +2462,7 @@ static mfs_status solve_impl(mfs_ctx* c, const mfs_solve_opts* opts, mfs_solve_i
   }
   CHECK_LAUNCH(c);
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if ((s = check_tc_timeout(c)) != MFS_OK) return s;
   c->solved = true;
   if (info) {
     info->iters = iters;
@@ -2216,8 +2606,8 @@ mfs_status mfs_get_rhs(mfs_ctx* c, double* wb) {
 static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* in1, const double* in2, double* out) {
   mfs_status s = check_state(c, 2);
   if (s != MFS_OK) return s;
-  if (precision != MFS_FP64 && precision != MFS_MIXED && precision != MFS_FP32)
-    return c->fail(MFS_ERR_ARG, "precision must be MFS_FP64, MFS_MIXED or MFS_FP32");
+  if (precision != MFS_FP64 && precision != MFS_MIXED && precision != MFS_FP32 && precision != MFS_MIXED_PASS)
+    return c->fail(MFS_ERR_ARG, "precision must be MFS_FP64, MFS_MIXED, MFS_FP32 or MFS_MIXED_PASS");
   if (!in1 || !out || (which == 2 && !in2)) return c->fail(MFS_ERR_ARG, "null array");
   if (which != 2 && !c->factored) return c->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
   const long long n = c->n, nu = c->n_unk;
@@ -2230,11 +2620,12 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
   if (which == 2) CUDA_TRY(c, cudaMemcpyAsync(c->d_mu, in2, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
   double* dout = which == 1 ? c->d_lh64 : c->d_w64;
   if (precision != MFS_FP32) {
-    c->dw_pairs = (precision == MFS_MIXED);
+    c->dw_pairs = (precision == MFS_MIXED || precision == MFS_MIXED_PASS);
+    c->dw_fast_a = c->ff_pass = (precision == MFS_MIXED_PASS);
     if (which == 0) apply_op<double>(c, c->d_mu, c->d_w64);
     else if (which == 1) precond<double>(c, c->d_mu, c->d_lh64);
     else pairs_step<double>(c, c->d_lam, c->d_mu, c->d_w64);
-    c->dw_pairs = c->dw_fast_a = false;
+    c->dw_pairs = c->dw_fast_a = c->ff_pass = false;
   } else {
     launch_convert<double, float>(len1, d1, 1.0, c->d_in32, c->stream);
     if (which == 0) {
@@ -2251,7 +2642,7 @@ static mfs_status run_step(mfs_ctx* c, int precision, int which, const double* i
   CUDA_TRY(c, cudaMemcpyAsync(out, dout, sizeof(double) * lenout, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (c->prof) collect_events(c);
-  return MFS_OK;
+  return check_tc_timeout(c);
 }
 
 mfs_status mfs_batch_solve(int n_problems, mfs_ctx* const* ctxs, const mfs_solve_opts* opts, mfs_solve_info* infos) {

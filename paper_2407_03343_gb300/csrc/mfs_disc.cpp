@@ -61,11 +61,25 @@ void perp_frame(const double* e, double* e1, double* e2) {
 
 }  // namespace
 
+void fibonacci_sphere(int n, double r, std::vector<double>& out) {
+  out.assign(3 * (size_t)n, 0.0);
+  for (int j = 1; j <= n; ++j) {
+    double d[3];
+    fib_direction(j, n, 1.0 - (2.0 * j - 1.0) / n, d);
+    for (int q = 0; q < 3; ++q) out[3 * (size_t)(j - 1) + q] = r * d[q];
+  }
+}
+
 mfs_status build_discretisation(const double* centres, int P, double a, const mfs_params& p,
                                 HostDisc& out, std::string& err) {
   if (P <= 0 || p.n_proxy <= 0 || p.m_basic <= 0 || !(a > 0) || !(p.r_proxy > 0) || p.r_proxy >= 1.0 ||
       p.alpha1 < 0 || p.alpha2 < 0 || !(p.visc > 0) || p.nim_max < 0 || p.nim_min < 0 || p.nim_min > p.nim_max) {
     err = "invalid discretisation parameters";
+    return MFS_ERR_ARG;
+  }
+  if (p.far_dist < 0 || (p.far_dist > 0 && (p.far_n_eq < 4 || !(p.far_r_eq > 0) || !(p.far_r_chk > p.far_r_eq) ||
+                                             p.far_dist < p.far_r_chk + 1.0 || !(p.far_eps > 0) || p.far_eps >= 1))) {
+    err = "invalid far-field parameters (need n_eq >= 4, 0 < r_eq < r_chk, far_dist >= r_chk + 1, 0 < eps < 1)";
     return MFS_ERR_ARG;
   }
   HostDisc d;

@@ -47,6 +47,10 @@ struct HostDisc {
 mfs_status build_discretisation(const double* centres, int P, double a, const mfs_params& p,
                                 HostDisc& out, std::string& err);
 
+// n points of the quasi-uniform Fibonacci grid (the basic-grid construction of Sec. 2.1) on the
+// sphere of radius r about the origin, 3 n values.
+void fibonacci_sphere(int n, double r, std::vector<double>& out);
+
 // ---------------------------------------------------------------- device-side views
 
 // Target (collocation) nodes grouped by sphere, processed in tiles that never straddle
@@ -82,8 +86,50 @@ struct SourceSet {
   double* cen64 = nullptr;       // 3P
 };
 
+// Far-field representation of the other spheres' sources in the GMRES passes (built when
+// mfs_params.far_dist > 0): for target sphere k the spheres within far_dist of it ("near") are
+// summed directly in double-float; every other sphere k' acts through n_eq equivalent
+// Stokeslets on a sphere about c_k' whose strengths q_k' = Q_f mu_k' come from one FP32
+// matrix per distinct one-body factor (Q_f maps the sphere's collocation data to the
+// equivalent sources reproducing the field of B_f^+ mu outside the check sphere).
+struct FarField {
+  int n_eq = 0;
+  float4* eq32 = nullptr;   // equivalent-source positions relative to the owner centre
+  int* near_off = nullptr;  // P+1: CSR of the near spheres of each sphere, ascending
+  int* near_idx = nullptr;
+  int* excl_off = nullptr;  // P+1: the near spheres and the sphere itself, ascending (far: the rest)
+  int* excl_idx = nullptr;
+  const float* q = nullptr; // equivalent strengths, 3 n_eq per sphere, sphere-major
+};
+
 // Kernels launched so far by the calling host thread (every launcher below counts itself).
 long long launches_on_this_thread();
+void note_launch();
+
+// Tensor-core product C = A X^T for the spheres sharing the basic factor (mfs_tc.cu): A (M x K)
+// and X (n_cap x K) as three bf16 slices each (row-major, leading dimension ldk = K rounded up to
+// the 64-element pipeline chunk, zero-padded), tensor maps prepared once.
+struct TcGemm {
+  int M = 0, K = 0, ldk = 0, n_cap = 0, nk = 0;
+  alignas(64) unsigned char maps[6][128];  // CUtensorMap of A0 A1 A2 X0 X1 X2
+  void* x_slices[3] = {nullptr, nullptr, nullptr};
+};
+int tc_ldk(int cols);
+// slices of a row-major FP64 matrix (rows x cols, leading dimension ld) into rows x ldk bf16 matrices
+void launch_split3_matrix(int rows, int cols, long long ld, const double* in, int ldk, void* s0, void* s1, void* s2,
+                          cudaStream_t st);
+void launch_split3_matrix_f32(int rows, int cols, long long ld, const float* in, int ldk, void* s0, void* s1, void* s2,
+                              cudaStream_t st);
+// tensor maps of the A slices (M rows) and X slices (n_cap rows), K columns; false if the driver
+// cannot encode them or the kernel's shared memory cannot be raised
+bool tc_prepare(TcGemm& g, const void* const a_slices[3], int M, const void* const x_slices[3], int n_cap, int K);
+// FP32 partial-sum scratch (floats) that launch_tc_gemm needs for ncols columns
+size_t tc_partial_floats(const TcGemm& g, int ncols);
+// column n = x[x_off[n] ...]: slices it, multiplies on the tensor cores, and writes
+// (A x_n)[m] to y32[y_off[n] + m] (FP32) or y2[y_off[n] + m] = (value, 0); err set on a wait timeout.
+// slice_x = false reuses the X slices the previous product over the same x wrote.
+void launch_tc_gemm(const TcGemm& g, int ncols, const double* x, const long long* x_off, const long long* y_off,
+                    float* y32, float2* y2, float* partial, int* err, bool slice_x, cudaStream_t st);
 
 // Kernel launchers (mfs_kernels.cu).  All run on `st`.
 template <typename T>
@@ -103,6 +149,15 @@ constexpr int kPairSplitTarget = 152 * 7;
 constexpr int kPairSplitMinSources = 64;
 constexpr int kPairMaxParts = 16;
 int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts);
+
+// Near part of the far-field split, double-float: out = mu + W sum over the near spheres of the
+// target's sphere (their proxies and image triples) of G lambda_hat.
+void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
+                          const double* mu, double* out, double visc, cudaStream_t st);
+// Far part, FP32 with compensated cross-tile sums: out += W sum over the far spheres of the
+// equivalent Stokeslets' field.  Returns the equivalent-source pairs evaluated.
+void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
+                      cudaStream_t st);
 
 // Many problems per launch (FP64 data): a device table of per-problem kernel arguments, a work
 // list of (problem, tile) pairs and a per-problem active flag.
@@ -148,6 +203,11 @@ void launch_split_dw(long long n, const double* in, float2* out, cudaStream_t st
 void launch_assemble_self(const HostDisc& hd, int k, const double* d_colloc_rel, const double* d_sqrtw,
                           const double* d_src_rel, const int* d_src_type, int n_src, double* B, int lda,
                           cudaStream_t st);
+
+// The same kernel matrix for m arbitrary targets (xrel, 3 m, row scale sqrtw, m) and n_src sources
+// (yrel, 3 n_src, types 0 S / 1 R / 2 D), column-major with leading dimension lda.
+void launch_assemble_block(int m, int n_src, const double* xrel, const double* sqrtw, const double* yrel,
+                           const int* type, double visc, double* B, long long lda, cudaStream_t st);
 
 // Krylov helpers.
 template <typename T>

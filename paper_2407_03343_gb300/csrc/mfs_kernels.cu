@@ -441,46 +441,33 @@ struct __align__(16) DWPos {
   float xl, yl, zl, pad1;
 };
 
-// Sources may be split over `nparts` CTAs per target tile (when there are too few tiles to
-// fill the GPU): part `part` takes a contiguous share of the tile's source list (the sources of
-// every other sphere) and, for nparts > 1, writes its scaled partial sum to
-// partial[part * pstride + 3 node + c] for pair_parts_reduce to finish.
+// Target nodes of one tile in double-float, with their running sums.
 template <int NT>
-__device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const int t, const int part, const int nparts,
-                                             double* __restrict__ partial, const long long pstride) {
-  __shared__ float4 sp[2 * kTileProxy];   // position hi, lo
-  __shared__ float4 sf[2 * kTileProxy];   // strength hi, lo
-  __shared__ float4 si[6 * kTileImg];     // image node: 12 hi values (3 float4), then 12 lo values (3 float4)
-
-  const int k = A.tile_sphere[t];
-  const int start = A.tile_start[t];
-  const int cnt = A.tile_count[t];
-  CentreShift64 sh;
-  sh.cen = A.cen64;
-  sh.init(k);
-
+struct DWTile {
   dw x[NT], y[NT], z[NT], ux[NT], uy[NT], uz[NT];
+};
+
+template <int NT>
+__device__ __forceinline__ void dw_load_targets(const PairArgs<double>& A, int start, int cnt, DWTile<NT>& T) {
 #pragma unroll
   for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     int node = start + (idx < cnt ? idx : cnt - 1);
     D4 p = A.tgt[node];
-    x[q] = dw_split(p.x);
-    y[q] = dw_split(p.y);
-    z[q] = dw_split(p.z);
-    ux[q] = uy[q] = uz[q] = dw{0.f, 0.f};
+    T.x[q] = dw_split(p.x);
+    T.y[q] = dw_split(p.y);
+    T.z[q] = dw_split(p.z);
+    T.ux[q] = T.uy[q] = T.uz[q] = dw{0.f, 0.f};
   }
-  const double far = 1e18;
+}
 
+// Proxy Stokeslets [r_lo, r_hi) of the flattened proxy index (sphere o = j / N, proxy j - o N),
+// staged through shared memory in tiles of kTileProxy; sphere k's own proxies carry no strength.
+template <int NT>
+__device__ __forceinline__ void dw_proxy_range(const PairArgs<double>& A, const CentreShift64& sh, int k, int r_lo,
+                                               int r_hi, float4* sp, float4* sf, DWTile<NT>& T) {
+  const double far = 1e18;
   const int total = A.P * A.N;
-  // the proxies before and after sphere k's own (this part's share of them), in tiles with
-  // exact trip counts
-  const int p_lo = k < 0 ? total : k * A.N, p_w = k < 0 ? 0 : A.N;
-  const long long p_eff = total - p_w;
-  const int pe0 = (int)(p_eff * part / nparts), pe1 = (int)(p_eff * (part + 1) / nparts);
-  for (int rr = 0; rr < 2; ++rr) {
-  const int r_lo = rr == 0 ? min(pe0, p_lo) : max(pe0, p_lo) + p_w;
-  const int r_hi = rr == 0 ? min(pe1, p_lo) : max(pe1, p_lo) + p_w;
   for (int s0 = r_lo; s0 < r_hi; s0 += kTileProxy) {
     const int ns = min(kTileProxy, r_hi - s0);
     __syncthreads();
@@ -513,33 +500,32 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
 #pragma unroll
       for (int q = 0; q < NT; ++q) {
-        dw dx = sub_pos(x[q], dw{ph.x, pl.x});
-        dw dy = sub_pos(y[q], dw{ph.y, pl.y});
-        dw dz = sub_pos(z[q], dw{ph.z, pl.z});
+        dw dx = sub_pos(T.x[q], dw{ph.x, pl.x});
+        dw dy = sub_pos(T.y[q], dw{ph.y, pl.y});
+        dw dz = sub_pos(T.z[q], dw{ph.z, pl.z});
         dw ir = rsqrt_u(norm2_u(dx, dy, dz));
         dw ir2 = mul_u(ir, ir);
         dw c = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
-        acc_u(ux[q], mul_u(ir, add_u(fx, mul_u(c, dx))));
-        acc_u(uy[q], mul_u(ir, add_u(fy, mul_u(c, dy))));
-        acc_u(uz[q], mul_u(ir, add_u(fz, mul_u(c, dz))));
+        acc_u(T.ux[q], mul_u(ir, add_u(fx, mul_u(c, dx))));
+        acc_u(T.uy[q], mul_u(ir, add_u(fy, mul_u(c, dy))));
+        acc_u(T.uz[q], mul_u(ir, add_u(fz, mul_u(c, dz))));
       }
     }
 #pragma unroll
     for (int q = 0; q < NT; ++q) {
-      ux[q] = two_sum(ux[q].h, ux[q].l);
-      uy[q] = two_sum(uy[q].h, uy[q].l);
-      uz[q] = two_sum(uz[q].h, uz[q].l);
+      T.ux[q] = two_sum(T.ux[q].h, T.ux[q].l);
+      T.uy[q] = two_sum(T.uy[q].h, T.uy[q].l);
+      T.uz[q] = two_sum(T.uz[q].h, T.uz[q].l);
     }
   }
-  }
+}
 
-  // image nodes before and after sphere k's own, this part's share
-  const int i_lo = k >= 0 ? A.img_off[k] : 0, i_w = k >= 0 ? A.img_off[k + 1] - i_lo : 0;
-  const long long i_eff = A.n_img - i_w;
-  const int ie0 = (int)(i_eff * part / nparts), ie1 = (int)(i_eff * (part + 1) / nparts);
-  for (int rr = 0; rr < 2; ++rr) {
-  const int r_lo = rr == 0 ? min(ie0, i_lo) : max(ie0, i_lo) + i_w;
-  const int r_hi = rr == 0 ? min(ie1, i_lo) : max(ie1, i_lo) + i_w;
+// Image nodes [r_lo, r_hi) (Stokeslet + rotlet + potential dipole at one position), staged in
+// tiles of kTileImg; sphere k's own nodes carry no strength.
+template <int NT>
+__device__ __forceinline__ void dw_image_range(const PairArgs<double>& A, const CentreShift64& sh, int k, int r_lo,
+                                               int r_hi, float4* si, DWTile<NT>& T) {
+  const double far = 1e18;
   for (int s0 = r_lo; s0 < r_hi; s0 += kTileImg) {
     const int ns = min(kTileImg, r_hi - s0);
     __syncthreads();
@@ -582,45 +568,50 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
       const dw qx{h2.y, l2.y}, qy{h2.z, l2.z}, qz{h2.w, l2.w};
 #pragma unroll
       for (int q = 0; q < NT; ++q) {
-        dw dx = sub_pos(x[q], px), dy = sub_pos(y[q], py), dz = sub_pos(z[q], pz);
+        dw dx = sub_pos(T.x[q], px), dy = sub_pos(T.y[q], py), dz = sub_pos(T.z[q], pz);
         dw ir = rsqrt_u(norm2_u(dx, dy, dz));
         dw ir2 = mul_u(ir, ir);
         dw ir3 = mul_u(ir, ir2);
         // Stokeslet
         dw cs = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
-        acc_u(ux[q], mul_u(ir, add_u(fx, mul_u(cs, dx))));
-        acc_u(uy[q], mul_u(ir, add_u(fy, mul_u(cs, dy))));
-        acc_u(uz[q], mul_u(ir, add_u(fz, mul_u(cs, dz))));
+        acc_u(T.ux[q], mul_u(ir, add_u(fx, mul_u(cs, dx))));
+        acc_u(T.uy[q], mul_u(ir, add_u(fy, mul_u(cs, dy))));
+        acc_u(T.uz[q], mul_u(ir, add_u(fz, mul_u(cs, dz))));
         // rotlet (t x r) / r^3
-        acc_u(ux[q], mul_u(ir3, add_u(mul_u(ty, dz), neg(mul_u(tz, dy)))));
-        acc_u(uy[q], mul_u(ir3, add_u(mul_u(tz, dx), neg(mul_u(tx, dz)))));
-        acc_u(uz[q], mul_u(ir3, add_u(mul_u(tx, dy), neg(mul_u(ty, dx)))));
+        acc_u(T.ux[q], mul_u(ir3, add_u(mul_u(ty, dz), neg(mul_u(tz, dy)))));
+        acc_u(T.uy[q], mul_u(ir3, add_u(mul_u(tz, dx), neg(mul_u(tx, dz)))));
+        acc_u(T.uz[q], mul_u(ir3, add_u(mul_u(tx, dy), neg(mul_u(ty, dx)))));
         // potential dipole -d / r^3 + 3 (d.r) r / r^5
         dw c3 = times3_u(mul_u(mul_u(dot3_u(dx, dy, dz, qx, qy, qz), ir3), ir2));
-        acc_u(ux[q], mul_u(c3, dx));
-        acc_u(uy[q], mul_u(c3, dy));
-        acc_u(uz[q], mul_u(c3, dz));
-        acc_u(ux[q], neg(mul_u(ir3, qx)));
-        acc_u(uy[q], neg(mul_u(ir3, qy)));
-        acc_u(uz[q], neg(mul_u(ir3, qz)));
+        acc_u(T.ux[q], mul_u(c3, dx));
+        acc_u(T.uy[q], mul_u(c3, dy));
+        acc_u(T.uz[q], mul_u(c3, dz));
+        acc_u(T.ux[q], neg(mul_u(ir3, qx)));
+        acc_u(T.uy[q], neg(mul_u(ir3, qy)));
+        acc_u(T.uz[q], neg(mul_u(ir3, qz)));
       }
     }
 #pragma unroll
     for (int q = 0; q < NT; ++q) {
-      ux[q] = two_sum(ux[q].h, ux[q].l);
-      uy[q] = two_sum(uy[q].h, uy[q].l);
-      uz[q] = two_sum(uz[q].h, uz[q].l);
+      T.ux[q] = two_sum(T.ux[q].h, T.ux[q].l);
+      T.uy[q] = two_sum(T.uy[q].h, T.uy[q].l);
+      T.uz[q] = two_sum(T.uz[q].h, T.uz[q].l);
     }
   }
-  }
+}
 
+// out = mu + sqrt(w) scale u per node (or the scaled partial sum of this source part, or the
+// plain scaled sum when mu is null)
+template <int NT>
+__device__ __forceinline__ void dw_write_out(const PairArgs<double>& A, int start, int cnt, const DWTile<NT>& T,
+                                             int part, int nparts, double* __restrict__ partial, long long pstride) {
 #pragma unroll
   for (int q = 0; q < NT; ++q) {
     int idx = threadIdx.x + q * kPairThreads;
     if (idx < cnt) {
       long long node = start + idx;
       double sw = A.tgt[node].w;
-      double gx = dw_join(ux[q]) * A.scale, gy = dw_join(uy[q]) * A.scale, gz = dw_join(uz[q]) * A.scale;
+      double gx = dw_join(T.ux[q]) * A.scale, gy = dw_join(T.uy[q]) * A.scale, gz = dw_join(T.uz[q]) * A.scale;
       if (nparts > 1) {
         double* o = partial + part * pstride + 3 * node;
         o[0] = gx;
@@ -639,6 +630,177 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
   }
 }
 
+// Sources may be split over `nparts` CTAs per target tile (when there are too few tiles to
+// fill the GPU): part `part` takes a contiguous share of the tile's source list (the sources of
+// every other sphere) and, for nparts > 1, writes its scaled partial sum to
+// partial[part * pstride + 3 node + c] for pair_parts_reduce to finish.
+template <int NT>
+__device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const int t, const int part, const int nparts,
+                                             double* __restrict__ partial, const long long pstride) {
+  __shared__ float4 sp[2 * kTileProxy];   // position hi, lo
+  __shared__ float4 sf[2 * kTileProxy];   // strength hi, lo
+  __shared__ float4 si[6 * kTileImg];     // image node: 12 hi values (3 float4), then 12 lo values (3 float4)
+
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift64 sh;
+  sh.cen = A.cen64;
+  sh.init(k);
+  DWTile<NT> T;
+  dw_load_targets<NT>(A, start, cnt, T);
+
+  const int total = A.P * A.N;
+  // the proxies before and after sphere k's own (this part's share of them), in tiles with
+  // exact trip counts
+  const int p_lo = k < 0 ? total : k * A.N, p_w = k < 0 ? 0 : A.N;
+  const long long p_eff = total - p_w;
+  const int pe0 = (int)(p_eff * part / nparts), pe1 = (int)(p_eff * (part + 1) / nparts);
+  dw_proxy_range<NT>(A, sh, k, min(pe0, p_lo), min(pe1, p_lo), sp, sf, T);
+  dw_proxy_range<NT>(A, sh, k, max(pe0, p_lo) + p_w, max(pe1, p_lo) + p_w, sp, sf, T);
+
+  // image nodes before and after sphere k's own, this part's share
+  const int i_lo = k >= 0 ? A.img_off[k] : 0, i_w = k >= 0 ? A.img_off[k + 1] - i_lo : 0;
+  const long long i_eff = A.n_img - i_w;
+  const int ie0 = (int)(i_eff * part / nparts), ie1 = (int)(i_eff * (part + 1) / nparts);
+  dw_image_range<NT>(A, sh, k, min(ie0, i_lo), min(ie1, i_lo), si, T);
+  dw_image_range<NT>(A, sh, k, max(ie0, i_lo) + i_w, max(ie1, i_lo) + i_w, si, T);
+
+  dw_write_out<NT>(A, start, cnt, T, part, nparts, partial, pstride);
+}
+
+// The near part of the far-field split: only the spheres of the target sphere's near list
+// (ascending; runs of consecutive spheres are staged as one range).
+template <int NT>
+__device__ __forceinline__ void pair_tile_dw_near(const PairArgs<double>& A, const int* __restrict__ near_off,
+                                                  const int* __restrict__ near_idx, const int t) {
+  __shared__ float4 sp[2 * kTileProxy];
+  __shared__ float4 sf[2 * kTileProxy];
+  __shared__ float4 si[6 * kTileImg];
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift64 sh;
+  sh.cen = A.cen64;
+  sh.init(k);
+  DWTile<NT> T;
+  dw_load_targets<NT>(A, start, cnt, T);
+  const int a1 = near_off[k + 1];
+  for (int a = near_off[k]; a < a1;) {
+    const int o0 = near_idx[a];
+    int o1 = o0;
+    while (a + 1 < a1 && near_idx[a + 1] == o1 + 1) {
+      ++a;
+      ++o1;
+    }
+    ++a;
+    dw_proxy_range<NT>(A, sh, k, o0 * A.N, (o1 + 1) * A.N, sp, sf, T);
+    dw_image_range<NT>(A, sh, k, A.img_off[o0], A.img_off[o1 + 1], si, T);
+  }
+  dw_write_out<NT>(A, start, cnt, T, 0, 1, nullptr, 0);
+}
+
+// ------------------------------------------------------------------ far-field kernel (FP32)
+constexpr int kTileFar = 256;  // equivalent sources staged per round
+
+struct FarArgs {
+  const float4* tgt;     // (x - c_k, sqrt w) per node, FP32
+  const double* tgt64;   // the same in FP64 (sqrt w taken from here)
+  const int* tile_sphere;
+  const int* tile_start;
+  const int* tile_count;
+  const float4* eq;      // n_eq equivalent-source positions relative to the owner centre
+  int n_eq, P;
+  const int* excl_off;
+  const int* excl_idx;
+  const float* cen_hi;
+  const float* cen_lo;
+  const float* q;        // 3 n_eq strengths per sphere
+  double* out;
+  float scale;           // 1 / (8 pi mu)
+};
+
+// out += sqrt(w) scale sum over every sphere outside the target sphere's exclusion list (its
+// near spheres and itself) of the Stokeslet field of its equivalent sources.  The excluded
+// spheres split the flattened equivalent-source index into runs, each staged in tiles.
+template <int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A) {
+  __shared__ float4 sp[kTileFar];
+  __shared__ float4 sf[kTileFar];
+  const int t = blockIdx.x;
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift32 sh;
+  sh.hi = A.cen_hi;
+  sh.lo = A.cen_lo;
+  sh.init(k);
+  float x[NT], y[NT], z[NT], ux[NT], uy[NT], uz[NT], sx[NT], sy[NT], sz[NT], cx[NT], cy[NT], cz[NT];
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    float4 p = A.tgt[start + (idx < cnt ? idx : cnt - 1)];
+    x[q] = p.x; y[q] = p.y; z[q] = p.z;
+    ux[q] = uy[q] = uz[q] = sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = 0.f;
+  }
+  const int e1 = A.excl_off[k + 1];
+  int prev = -1;
+  for (int a = A.excl_off[k]; a <= e1; ++a) {
+    const int nxt = a < e1 ? A.excl_idx[a] : A.P;
+    const int lo = (prev + 1) * A.n_eq, hi = nxt * A.n_eq;
+    prev = nxt;
+    for (int s0 = lo; s0 < hi; s0 += kTileFar) {
+      const int ns = min(kTileFar, hi - s0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < ns; i += kPairThreads) {
+        const int j = s0 + i;
+        const int o = j / A.n_eq;
+        const int e = j - o * A.n_eq;
+        const float4 z0 = A.eq[e];
+        sp[i] = make_float4(z0.x + sh.d(o, 0), z0.y + sh.d(o, 1), z0.z + sh.d(o, 2), 0.f);
+        const float* g = A.q + 3LL * j;
+        sf[i] = make_float4(g[0], g[1], g[2], 0.f);
+      }
+      __syncthreads();
+#pragma unroll 2
+      for (int j = 0; j < ns; ++j) {
+        const float4 p = sp[j];
+        const float4 f = sf[j];
+#pragma unroll
+        for (int q = 0; q < NT; ++q) {
+          float dx = x[q] - p.x, dy = y[q] - p.y, dz = z[q] - p.z;
+          float r2 = dx * dx + dy * dy + dz * dz;
+          float ir = rsqrtf(r2);
+          float ir2 = ir * ir;
+          float rf = dx * f.x + dy * f.y + dz * f.z;
+          float c = rf * ir2;
+          ux[q] += ir * (f.x + c * dx);
+          uy[q] += ir * (f.y + c * dy);
+          uz[q] += ir * (f.z + c * dz);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        comp_add(sx[q], cx[q], ux[q]);
+        comp_add(sy[q], cy[q], uy[q]);
+        comp_add(sz[q], cz[q], uz[q]);
+        ux[q] = uy[q] = uz[q] = 0.f;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    if (idx < cnt) {
+      long long node = start + idx;
+      double sw = A.tgt64[4 * node + 3] * (double)A.scale;
+      A.out[3 * node] += sw * ((double)sx[q] + (double)cx[q]);
+      A.out[3 * node + 1] += sw * ((double)sy[q] + (double)cy[q]);
+      A.out[3 * node + 2] += sw * ((double)sz[q] + (double)cz[q]);
+    }
+  }
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_kernel(PairArgs<T> A) {
   pair_tile<T, NT>(A, blockIdx.x);
@@ -647,6 +809,11 @@ template <int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double> A, int nparts, double* partial,
                                                                 long long pstride) {
   pair_tile_dw<NT>(A, blockIdx.x / nparts, blockIdx.x % nparts, nparts, partial, pstride);
+}
+template <int NT>
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_near_kernel(PairArgs<double> A, const int* near_off,
+                                                                     const int* near_idx) {
+  pair_tile_dw_near<NT>(A, near_off, near_idx, blockIdx.x);
 }
 // out = mu + sqrt(w) * (sum of the parts), or the plain sum when mu is null; parts added in order
 __global__ void pair_parts_reduce_kernel(long long n3, const D4* __restrict__ tgt, int nparts,
@@ -1322,6 +1489,7 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 }  // namespace
 
 long long launches_on_this_thread() { return t_launches; }
+void note_launch() { ++t_launches; }
 
 template <typename T>
 void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu, T* out, double visc,
@@ -1361,6 +1529,41 @@ void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* la
     ++t_launches;
     pair_parts_reduce_kernel<<<grid_for(n3, 256), 256, 0, st>>>(n3, A.tgt, parts, partial, n3, mu, out);
   }
+}
+
+void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
+                          const double* mu, double* out, double visc, cudaStream_t st) {
+  if (tg.n_tiles == 0) return;
+  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
+  ++t_launches;
+  if (nt == 4) pairs_dw_near_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx);
+  else pairs_dw_near_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx);
+}
+
+void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
+                      cudaStream_t st) {
+  if (tg.n_tiles == 0 || ff.n_eq == 0) return;
+  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  FarArgs A;
+  A.tgt = tg.pos32;
+  A.tgt64 = tg.pos64;
+  A.tile_sphere = nt == 4 ? tg.tile_sphere : tg.tile1_sphere;
+  A.tile_start = nt == 4 ? tg.tile_start : tg.tile1_start;
+  A.tile_count = nt == 4 ? tg.tile_count : tg.tile1_count;
+  A.eq = ff.eq32;
+  A.n_eq = ff.n_eq;
+  A.P = src.P;
+  A.excl_off = ff.excl_off;
+  A.excl_idx = ff.excl_idx;
+  A.cen_hi = src.cen_hi;
+  A.cen_lo = src.cen_lo;
+  A.q = ff.q;
+  A.out = out;
+  A.scale = (float)(1.0 / (8.0 * kPi * visc));
+  ++t_launches;
+  if (nt == 4) pairs_far_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
+  else pairs_far_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A);
 }
 
 size_t pair_args64_bytes() { return sizeof(PairArgs<double>); }
@@ -1541,6 +1744,17 @@ double launch_fma_probe(int which, int blocks, int iters, void* sink, cudaStream
   if (which == 0) fma_probe_kernel<float><<<blocks, 256, 0, st>>>(iters, 0.9999f, 1e-4f, static_cast<float*>(sink));
   else fma_probe_kernel<double><<<blocks, 256, 0, st>>>(iters, 0.9999, 1e-4, static_cast<double*>(sink));
   return 2.0 * 8.0 * 16.0 * (double)iters * (double)blocks * 256.0;  // flops
+}
+
+void launch_assemble_block(int m, int n_src, const double* xrel, const double* sqrtw, const double* yrel,
+                           const int* type, double visc, double* B, long long lda, cudaStream_t st) {
+  long long tot = (long long)m * n_src;
+  int threads = 256;
+  long long blocks = (tot + threads - 1) / threads;
+  if (blocks == 0) return;
+  ++t_launches;
+  assemble_self_kernel<<<(unsigned)blocks, threads, 0, st>>>(m, n_src, xrel, sqrtw, yrel, type, 1.0 / (8.0 * kPi * visc),
+                                                             B, lda);
 }
 
 void launch_assemble_self(const HostDisc& hd, int k, const double* d_colloc_rel, const double* d_sqrtw,

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "mfs.h")
 FP64 = 0
 MIXED = 1
 FP32 = 2
+MIXED_PASS = 3   # single-step entry points: the operator of the MIXED GMRES passes
 RESIDUAL_AUTO = 0
 RESIDUAL_FP64 = 1
 RESIDUAL_SOLVE = 2
@@ -35,7 +36,9 @@ class Params(C.Structure):
                 ("beta1", C.c_double), ("beta2", C.c_double), ("eps_trunc", C.c_double),
                 ("nim_a", C.c_double), ("nim_b", C.c_double), ("nim_cut", C.c_double),
                 ("nim_max", C.c_int), ("nim_fixed", C.c_int), ("left_precond", C.c_int),
-                ("visc", C.c_double), ("build_factors", C.c_int), ("nim_min", C.c_int)]
+                ("visc", C.c_double), ("build_factors", C.c_int), ("nim_min", C.c_int),
+                ("far_dist", C.c_double), ("far_n_eq", C.c_int), ("far_r_eq", C.c_double),
+                ("far_r_chk", C.c_double), ("far_eps", C.c_double), ("tensor_step1", C.c_int)]
 
 
 class SolveOpts(C.Structure):
@@ -52,7 +55,8 @@ class SolveInfo(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("P", C.c_int), ("n_contacts", C.c_int), ("n_colloc", C.c_int),
                 ("n_proxy_total", C.c_int), ("n_image_nodes", C.c_int), ("n_unknowns", C.c_int),
-                ("n_factors", C.c_int), ("pairs_fp", C.c_longlong)]
+                ("n_factors", C.c_int), ("pairs_fp", C.c_longlong), ("pairs_near_fp", C.c_longlong),
+                ("pairs_far_eq", C.c_longlong)]
 
 
 class Timing(C.Structure):
@@ -62,7 +66,8 @@ class Timing(C.Structure):
                 ("gemv_ms", C.c_double), ("gemv_bytes", C.c_double),
                 ("by_kind_launches", C.c_longlong * 3), ("by_kind_ms", C.c_double * 3),
                 ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3),
-                ("krylov_launches", C.c_longlong), ("krylov_ms", C.c_double), ("krylov_bytes", C.c_double)]
+                ("krylov_launches", C.c_longlong), ("krylov_ms", C.c_double), ("krylov_bytes", C.c_double),
+                ("far_launches", C.c_longlong), ("far_ms", C.c_double), ("far_pairs", C.c_longlong)]
 
 
 class MfsError(RuntimeError):
