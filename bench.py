@@ -62,6 +62,14 @@ def parse():
     ap.add_argument("--tol", type=float, default=SWEEP_TOL, help="GMRES tolerance of the timed solves")
     ap.add_argument("--kernel-case", type=int, default=0,
                     help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
+    ap.add_argument("--profile-case", default="", choices=["", "far", "tensor"],
+                    help="profiling case: 'far' = pass-operator applies on a 24-sphere suspension with the far field, "
+                         "'tensor' = the same on 60 contact-free spheres with the tensor-core step 1; then exit")
+    ap.add_argument("--suspension", type=int, default=200,
+                    help="spheres of the far-field suspension solve among the extras (0 = skip)")
+    ap.add_argument("--cluster-example", type=int, default=0,
+                    help="run only the fixed-cluster example (Sec. 4, Ex. 2) with this many spheres and the far "
+                         "field, print its JSON and exit")
     return ap.parse_args()
 
 
@@ -234,6 +242,138 @@ def suspension_kernel_rates(device, fp32_peak):
     return out
 
 
+FAR = dict(far_dist=4.0, far_n_eq=300, far_r_eq=1.0, far_r_chk=2.0, far_eps=1e-6)
+
+
+def suspension_solve(device, P=200, tol=SWEEP_TOL):
+    """The random suspension (P unit spheres at volume fraction 0.2, near contacts at gaps
+    log-uniform in [1e-3, 1e-1], N = 800, M0 = 1600, random rigid motions) solved in MIXED
+    precision with the far field in the GMRES passes (spheres more than 4 radii apart through 300
+    equivalent Stokeslets) and the exact double-float operator in the refinement residual.  The
+    solve is timed with CUDA events on the context's stream; the operator applies of the passes,
+    of the exact double-float operator and of the plain FP64 operator are timed per launch."""
+    import torch
+    from paper_2407_03343_gb300 import mfs, workloads
+    st = torch.cuda.Stream()
+    ctx = mfs.Context(device, stream=st.cuda_stream)
+    centres = workloads.suspension(P, 0.2, seed=3)
+    ctx.set_spheres(centres)
+    t0 = time.perf_counter()
+    ctx.build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC, **FAR)
+    setup = time.perf_counter() - t0
+    s = ctx.sizes()
+    v, w = workloads.rigid_velocities(P, seed=1)
+    ctx.set_rigid_velocities(v, w)
+    ctx.set_profiling(True)
+    mu = ctx.rhs()
+    applies = {}
+    for name, prec, reps in (("pass_far_field", mfs.MIXED_PASS, 3), ("exact_double_float", mfs.MIXED, 2),
+                             ("exact_fp64", mfs.FP64, 1)):
+        ctx.apply_operator(mu, prec)
+        ctx.timing(reset=True)
+        for _ in range(reps):
+            ctx.apply_operator(mu, prec)
+        t = ctx.timing(reset=True)
+        applies[name] = {"pair_ms": t.pair_ms / reps, "far_ms": t.far_ms / reps, "gemv_ms": t.gemv_ms / reps,
+                         "near_pairs": t.pair_interactions / reps, "far_equivalent_pairs": t.far_pairs / reps}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    info = ctx.solve(precision="mixed", tol=tol, max_iter=4000, allow_not_converged=True)
+    e1.record(st)
+    e1.synchronize()
+    t = ctx.timing(reset=True)
+    F, T = ctx.forces_torques()
+    solve_s = e0.elapsed_time(e1) / 1000.0
+    out = {"spheres": P, "contacts": s.n_contacts, "nodes": s.n_colloc, "setup_s": setup,
+           "pairs_exact_per_apply": s.pairs_fp, "pairs_near_per_apply": s.pairs_near_fp,
+           "equivalent_pairs_per_apply": s.pairs_far_eq, "device_GB": ctx.memory_in_use() / 1e9,
+           "applies_ms": applies, "solve_s": solve_s, "iters": info.iters, "refinements": info.refinements,
+           "rel_residual_exact_operator": info.rel_residual, "converged": info.converged, "tol": tol,
+           "near_pairs_per_s": t.pair_interactions / (t.pair_ms / 1000.0) if t.pair_ms else None,
+           "equivalent_pairs_per_s": t.far_pairs / (t.far_ms / 1000.0) if t.far_ms else None,
+           "near_ms": t.pair_ms, "far_ms": t.far_ms, "gemv_ms": t.gemv_ms,
+           "ft_finite": bool(np.all(np.isfinite(F)) and np.all(np.isfinite(T))),
+           "timing": "solve: CUDA events on the context stream, one solve; applies: per-launch CUDA events"}
+    ctx.close()
+    return out
+
+
+def cluster_example(device, P=100, delta=1e-2, r_proxy=0.75, far=False):
+    """Sec. 4, Ex. 2: a cluster grown so that every sphere has a neighbour delta away, held fixed
+    in the shear flow u_inf = (5 y, 0, 0); basic method (no images, as the paper runs it), N = 686,
+    M0 = 823, GMRES tolerance 1e-6.  Every sphere shares the basic factor (one SVD), so step 1 of
+    the passes runs on the tensor cores; with far=True the passes use the far field as well.
+    Reports the solve (CUDA events), its iterations against Table cluster_table, the largest
+    relative surface residual (eq. residual) on the check grids of up to 20 spheres, and
+    max |lambda|."""
+    import torch
+    from paper_2407_03343_gb300 import mfs, workloads
+    centres = workloads.cluster(P, delta, seed=1)
+    st = torch.cuda.Stream()
+    ctx = mfs.Context(device, stream=st.cuda_stream)
+    ctx.set_spheres(centres)
+    kw = dict(n_proxy=686, r_proxy=r_proxy, m_basic=823, nim_fixed=0)
+    if far:
+        kw.update(FAR)
+    t0 = time.perf_counter()
+    ctx.build(**kw)
+    setup = time.perf_counter() - t0
+    U, E, Om = workloads.shear_flow(5.0)
+    ctx.set_background_flow(U=U, E=E, Omega=Om)
+    ctx.set_rigid_velocities(np.zeros((P, 3)), np.zeros((P, 3)))
+    ctx.set_profiling(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    info = ctx.solve(precision="mixed", tol=1e-6, allow_not_converged=True)
+    e1.record(st)
+    e1.synchronize()
+    t = ctx.timing(reset=True)
+    # check grid: the 500-point Fibonacci grid of the spheres, axes permuted (y, z, x)
+    n = 500
+    j = np.arange(1, n + 1)
+    ct = 1.0 - (2.0 * j - 1.0) / n
+    ph = np.mod(2.0 * np.pi * j / ((1.0 + 5.0 ** 0.5) / 2.0), 2.0 * np.pi)
+    st_ = np.sqrt(1.0 - ct * ct)
+    chk = np.stack([st_ * np.cos(ph), st_ * np.sin(ph), ct], axis=1)[:, [1, 2, 0]]
+    ks = np.linspace(0, P - 1, min(P, 20)).astype(int)
+    x = np.concatenate([centres[k] + chk for k in ks])
+    u = ctx.eval_velocity(x)
+    ubc = -(U[None, :] + x @ E.T + np.cross(Om[None, :], x))
+    eres = float((np.linalg.norm(u - ubc, axis=1) / np.linalg.norm(ubc, axis=1)).max())
+    lam = ctx.strengths()
+    s = ctx.sizes()
+    out = {"spheres": P, "delta": delta, "r_proxy": r_proxy, "far_field": far, "setup_s": setup,
+           "solve_s": e0.elapsed_time(e1) / 1000.0, "iters": info.iters, "converged": info.converged,
+           "rel_residual": info.rel_residual, "eps_res_max_sampled": eres, "spheres_checked": int(len(ks)),
+           "lambda_max": float(np.abs(lam).max()), "dof": 3 * s.n_colloc, "factors": s.n_factors,
+           "near_ms": t.pair_ms, "far_ms": t.far_ms, "gemv_ms": t.gemv_ms,
+           "paper_P100_iters": {"1e-2,0.75": 92, "1e-3,0.75": 122, "1e-3,0.65": 116},
+           "paper_P2000_iters": {"1e-2,0.75": 144, "1e-3,0.75": 176, "1e-3,0.65": 156},
+           "paper_cpu_time_h": {"P100": 0.51, "P2000": 12.8}}
+    ctx.close()
+    return out
+
+
+def profile_case(kind, device):
+    """Small cases for ncu captures of the far-field and tensor-core kernels (two pass applies)."""
+    from paper_2407_03343_gb300 import mfs, workloads
+    ctx = mfs.Context(device)
+    if kind == "far":
+        # 24 spheres at volume fraction 0.08, N = 400, M0 = 800: a few GB on the device
+        ctx.set_spheres(workloads.suspension(24, 0.08, seed=3))
+        ctx.build(n_proxy=400, r_proxy=R_PROXY, m_basic=800, **FAR)
+    else:
+        g = np.arange(4) * 3.0
+        c = np.array([[x, y, z] for x in g for y in g for z in g])[:60]
+        ctx.set_spheres(c)
+        ctx.build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC, tensor_step1=2)
+    mu = ctx.rhs()
+    for _ in range(2):
+        ctx.apply_operator(mu, mfs.MIXED_PASS)
+    ctx.close()
+    print(json.dumps({"profile_case": kind}))
+
+
 def batched_suspensions(device, n_problems=16, p_hi=8):
     """Many small independent suspensions (P_i log-uniform in [2, p_hi], volume fraction
     U(0.05, 0.3), gaps of attached spheres log-uniform in [1e-3, 1e-1]; N = 400, M0 = 800,
@@ -354,6 +494,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     mfs.lib()
+    if args.profile_case:
+        profile_case(args.profile_case, local)
+        return 0
+    if args.cluster_example:
+        print(json.dumps({"cluster_example": cluster_example(local, args.cluster_example, far=True)}))
+        return 0
 
     gaps = workloads.gap_sweep_gaps()
     streams = [torch.cuda.Stream() for _ in gaps]
@@ -579,6 +725,9 @@ def main():
         extras["oracle_solve"] = oracle_solve_sample()
         extras["pair_kernels_200_spheres"] = suspension_kernel_rates(local, fp32_peak)
         extras["batched_suspensions"] = batched_suspensions(local)
+        extras["cluster_shear_P100"] = cluster_example(local, 100)
+        if args.suspension > 0:
+            extras["suspension_far_field_solve"] = suspension_solve(local, args.suspension, args.tol)
 
     if rank == 0:
         line = {"metric": "Stokeslet pair-interactions/s", "value": value, "unit": "pair-interactions/s",

@@ -346,7 +346,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
       // near spheres directly in double-float, the far ones through their equivalent sources,
       // whose strengths q = Q mu are formed from this apply's mu
       timed(c, c->ev_pair, [&] {
-        launch_pairs_dw_near(c->tg, c->src, c->ff, lam_hat, mu, out, c->hd.prm.visc, c->stream);
+        launch_pairs_dw_near(c->tg, c->src, c->ff, lam_hat, mu, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts,
+                             c->stream);
       });
       timed(c, c->ev_far, [&] {
         launch_convert<double, float>(c->n, mu, 1.0, c->d_mu32, c->stream);
@@ -357,7 +358,7 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
         } else {
           launch_gemv<float>(c->gQ, c->d_mu32, c->d_q, c->stream);
         }
-        launch_pairs_far(c->tg, c->src, c->ff, out, c->hd.prm.visc, c->stream);
+        launch_pairs_far(c->tg, c->src, c->ff, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream);
       });
       c->tm.pair_launches += 1;
       c->tm.pair_interactions += c->near_pairs_per_apply;

@@ -152,12 +152,15 @@ int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts);
 
 // Near part of the far-field split, double-float: out = mu + W sum over the near spheres of the
 // target's sphere (their proxies and image triples) of G lambda_hat.
+// Both split each tile's sources over up to max_parts CTAs (partial: max_parts * 3 n doubles, or
+// null for no split) so that the grid fills whole waves of resident CTAs; the parts are added in
+// a fixed order by a second kernel.
 void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
-                          const double* mu, double* out, double visc, cudaStream_t st);
+                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st);
 // Far part, FP32 with compensated cross-tile sums: out += W sum over the far spheres of the
-// equivalent Stokeslets' field.  Returns the equivalent-source pairs evaluated.
+// equivalent Stokeslets' field.
 void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
-                      cudaStream_t st);
+                      double* partial, int max_parts, cudaStream_t st);
 
 // Many problems per launch (FP64 data): a device table of per-problem kernel arguments, a work
 // list of (problem, tile) pairs and a per-problem active flag.

@@ -673,7 +673,9 @@ __device__ __forceinline__ void pair_tile_dw(const PairArgs<double>& A, const in
 // (ascending; runs of consecutive spheres are staged as one range).
 template <int NT>
 __device__ __forceinline__ void pair_tile_dw_near(const PairArgs<double>& A, const int* __restrict__ near_off,
-                                                  const int* __restrict__ near_idx, const int t) {
+                                                  const int* __restrict__ near_idx, const int t, const int part,
+                                                  const int nparts, double* __restrict__ partial,
+                                                  const long long pstride) {
   __shared__ float4 sp[2 * kTileProxy];
   __shared__ float4 sf[2 * kTileProxy];
   __shared__ float4 si[6 * kTileImg];
@@ -685,8 +687,10 @@ __device__ __forceinline__ void pair_tile_dw_near(const PairArgs<double>& A, con
   sh.init(k);
   DWTile<NT> T;
   dw_load_targets<NT>(A, start, cnt, T);
-  const int a1 = near_off[k + 1];
-  for (int a = near_off[k]; a < a1;) {
+  // this part's share of the near list
+  const int b0 = near_off[k], nn = near_off[k + 1] - b0;
+  const int a1 = b0 + (int)((long long)nn * (part + 1) / nparts);
+  for (int a = b0 + (int)((long long)nn * part / nparts); a < a1;) {
     const int o0 = near_idx[a];
     int o1 = o0;
     while (a + 1 < a1 && near_idx[a + 1] == o1 + 1) {
@@ -697,7 +701,7 @@ __device__ __forceinline__ void pair_tile_dw_near(const PairArgs<double>& A, con
     dw_proxy_range<NT>(A, sh, k, o0 * A.N, (o1 + 1) * A.N, sp, sf, T);
     dw_image_range<NT>(A, sh, k, A.img_off[o0], A.img_off[o1 + 1], si, T);
   }
-  dw_write_out<NT>(A, start, cnt, T, 0, 1, nullptr, 0);
+  dw_write_out<NT>(A, start, cnt, T, part, nparts, partial, pstride);
 }
 
 // ------------------------------------------------------------------ far-field kernel (FP32)
@@ -724,10 +728,11 @@ struct FarArgs {
 // near spheres and itself) of the Stokeslet field of its equivalent sources.  The excluded
 // spheres split the flattened equivalent-source index into runs, each staged in tiles.
 template <int NT>
-__global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A) {
+__global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A, int nparts, double* __restrict__ partial,
+                                                                 long long pstride) {
   __shared__ float4 sp[kTileFar];
   __shared__ float4 sf[kTileFar];
-  const int t = blockIdx.x;
+  const int t = blockIdx.x / nparts, part = blockIdx.x % nparts;
   const int k = A.tile_sphere[t];
   const int start = A.tile_start[t];
   const int cnt = A.tile_count[t];
@@ -743,12 +748,21 @@ __global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A) {
     x[q] = p.x; y[q] = p.y; z[q] = p.z;
     ux[q] = uy[q] = uz[q] = sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = 0.f;
   }
-  const int e1 = A.excl_off[k + 1];
+  const int e0 = A.excl_off[k], e1 = A.excl_off[k + 1];
+  // this part's share [f0, f1) of the far sources, counted in the order of the runs between
+  // excluded spheres
+  const long long n_far = (long long)(A.P - (e1 - e0)) * A.n_eq;
+  const long long f0 = n_far * part / nparts, f1 = n_far * (part + 1) / nparts;
+  long long before = 0;  // far sources in the runs before the current one
   int prev = -1;
-  for (int a = A.excl_off[k]; a <= e1; ++a) {
+  for (int a = e0; a <= e1; ++a) {
     const int nxt = a < e1 ? A.excl_idx[a] : A.P;
-    const int lo = (prev + 1) * A.n_eq, hi = nxt * A.n_eq;
+    const int run_lo = (prev + 1) * A.n_eq, run_hi = nxt * A.n_eq;
     prev = nxt;
+    const long long len = run_hi - run_lo;
+    const int lo = run_lo + (int)max(0LL, min(len, f0 - before));
+    const int hi = run_lo + (int)max(0LL, min(len, f1 - before));
+    before += len;
     for (int s0 = lo; s0 < hi; s0 += kTileFar) {
       const int ns = min(kTileFar, hi - s0);
       __syncthreads();
@@ -794,10 +808,30 @@ __global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A) {
     if (idx < cnt) {
       long long node = start + idx;
       double sw = A.tgt64[4 * node + 3] * (double)A.scale;
-      A.out[3 * node] += sw * ((double)sx[q] + (double)cx[q]);
-      A.out[3 * node + 1] += sw * ((double)sy[q] + (double)cy[q]);
-      A.out[3 * node + 2] += sw * ((double)sz[q] + (double)cz[q]);
+      const double gx = sw * ((double)sx[q] + (double)cx[q]), gy = sw * ((double)sy[q] + (double)cy[q]),
+                   gz = sw * ((double)sz[q] + (double)cz[q]);
+      if (nparts > 1) {
+        double* o = partial + part * pstride + 3 * node;
+        o[0] = gx;
+        o[1] = gy;
+        o[2] = gz;
+      } else {
+        A.out[3 * node] += gx;
+        A.out[3 * node + 1] += gy;
+        A.out[3 * node + 2] += gz;
+      }
     }
+  }
+}
+
+// out[e] (+)= the parts in order: with mu, out = mu + sqrt(w) * sum (the near kernel's unscaled
+// parts); without, out += sum (the far kernel's parts, already scaled)
+__global__ void parts_add_kernel(long long n3, const D4* __restrict__ tgt, int nparts, const double* __restrict__ partial,
+                                 long long pstride, const double* __restrict__ mu, double* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n3; e += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nparts; ++q) s += partial[q * pstride + e];
+    out[e] = mu ? mu[e] + tgt[e / 3].w * s : out[e] + s;
   }
 }
 
@@ -812,8 +846,9 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_kernel(PairArgs<double>
 }
 template <int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_dw_near_kernel(PairArgs<double> A, const int* near_off,
-                                                                     const int* near_idx) {
-  pair_tile_dw_near<NT>(A, near_off, near_idx, blockIdx.x);
+                                                                     const int* near_idx, int nparts, double* partial,
+                                                                     long long pstride) {
+  pair_tile_dw_near<NT>(A, near_off, near_idx, blockIdx.x / nparts, blockIdx.x % nparts, nparts, partial, pstride);
 }
 // out = mu + sqrt(w) * (sum of the parts), or the plain sum when mu is null; parts added in order
 __global__ void pair_parts_reduce_kernel(long long n3, const D4* __restrict__ tgt, int nparts,
@@ -1531,18 +1566,51 @@ void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* la
   }
 }
 
+// source parts per tile so that tiles x parts fill whole waves of the resident CTAs (ties: fewer)
+int wave_parts(long long tiles, const void* kernel, int max_parts) {
+  int per_sm = 0, sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPairThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  const double wave = (double)sms * per_sm;
+  int best = 1;
+  double best_eff = 0;
+  for (int p = 1; p <= max_parts; ++p) {
+    const double w = (double)tiles * p / wave;
+    const double eff = w / std::ceil(w);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = p;
+    }
+  }
+  return best;
+}
+
 void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
-                          const double* mu, double* out, double visc, cudaStream_t st) {
+                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st) {
   if (tg.n_tiles == 0) return;
   const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
   PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
+  const long long tiles = nt == 4 ? tg.n_tiles : tg.n_tiles1;
+  const int parts = partial ? wave_parts(tiles, nt == 4 ? (const void*)pairs_dw_near_kernel<4> : (const void*)pairs_dw_near_kernel<1>,
+                                         max_parts)
+                            : 1;
+  const long long n3 = 3LL * tg.n;
   ++t_launches;
-  if (nt == 4) pairs_dw_near_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx);
-  else pairs_dw_near_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx);
+  if (nt == 4)
+    pairs_dw_near_kernel<4><<<tiles * parts, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx, parts, partial, n3);
+  else
+    pairs_dw_near_kernel<1><<<tiles * parts, kPairThreads, 0, st>>>(A, ff.near_off, ff.near_idx, parts, partial, n3);
+  if (parts > 1) {
+    ++t_launches;
+    parts_add_kernel<<<grid_for(n3, 256), 256, 0, st>>>(n3, A.tgt, parts, partial, n3, mu, out);
+  }
 }
 
 void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
-                      cudaStream_t st) {
+                      double* partial, int max_parts, cudaStream_t st) {
   if (tg.n_tiles == 0 || ff.n_eq == 0) return;
   const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
   FarArgs A;
@@ -1561,9 +1629,19 @@ void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField&
   A.q = ff.q;
   A.out = out;
   A.scale = (float)(1.0 / (8.0 * kPi * visc));
+  const long long tiles = nt == 4 ? tg.n_tiles : tg.n_tiles1;
+  const int parts = partial ? wave_parts(tiles, nt == 4 ? (const void*)pairs_far_kernel<4> : (const void*)pairs_far_kernel<1>,
+                                         max_parts)
+                            : 1;
+  const long long n3 = 3LL * tg.n;
   ++t_launches;
-  if (nt == 4) pairs_far_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A);
-  else pairs_far_kernel<1><<<tg.n_tiles1, kPairThreads, 0, st>>>(A);
+  if (nt == 4) pairs_far_kernel<4><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  else pairs_far_kernel<1><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  if (parts > 1) {
+    ++t_launches;
+    parts_add_kernel<<<grid_for(n3, 256), 256, 0, st>>>(n3, reinterpret_cast<const D4*>(tg.pos64), parts, partial, n3,
+                                                        nullptr, out);
+  }
 }
 
 size_t pair_args64_bytes() { return sizeof(PairArgs<double>); }

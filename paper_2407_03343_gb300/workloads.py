@@ -13,6 +13,8 @@ suspension         P spheres in a cube of volume fraction phi, grown from unifor
                    kept at least min_gap apart.  Random rigid velocities ~ N(0, 1).
 batch              64 independent suspensions with P_i log-uniform in [2, 256],
                    phi_i ~ U(0.05, 0.3).
+cluster            fixed clusters grown so that every sphere has a neighbour exactly gap away
+                   (Sec. 4, Ex. 2; Sec. 5.2), with shear_flow / uniform_flow as background flows.
 """
 from __future__ import annotations
 
@@ -141,6 +143,19 @@ def cluster(P: int, gap: float, seed: int, radius: float = 1.0, max_tries: int =
             centres[n] = c
             n += 1
     return centres
+
+
+def shear_flow(rate: float = 5.0):
+    """Background shear flow of the fixed-cluster example (Sec. 4, Ex. 2) as (U, E, Omega) of
+    u_inf(x) = U + E x + Omega x x: E = (rate / 2) [[0, 1, 0], [1, 0, 0], [0, 0, 0]],
+    Omega = (0, 0, -rate / 2), i.e. u_inf = (rate y, 0, 0)."""
+    E = 0.5 * rate * np.array([[0.0, 1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    return np.zeros(3), E, np.array([0.0, 0.0, -0.5 * rate])
+
+
+def uniform_flow(speed: float = 5.0):
+    """Uniform background flow of the same example: u_inf = (speed, 0, 0)."""
+    return np.array([speed, 0.0, 0.0]), np.zeros((3, 3)), np.zeros(3)
 
 
 def rigid_velocities(P: int, seed: int):

@@ -5,7 +5,9 @@ approximation of that sum, so it is judged against the exact operator with a sta
   * the pass operator (Sigma^+ U^T from FP32, near spheres in double-float, far spheres through
     their FP32 equivalent sources) matches the oracle's exact operator to 1e-5 of its largest
     value on smooth data and on a Krylov-like vector; the same operator without the far field
-    (every sphere near) matches to 1e-7, and equals the all-pairs pass operator bit for bit;
+    (every sphere near) matches to 1e-7, and the all-pairs pass operator to 1e-10 (the same
+    double-float sums, in another order when the all-pairs kernel splits sources over CTAs, whose
+    rounding relative to the result grows with the cancellation of the Krylov-like vector);
   * a MIXED solve with the far field, whose refinement residual uses every pair exactly, meets
     the stated targets against the oracle's O3 solve (forces/torques 1e-5, velocity 1e-3).
 """
@@ -62,7 +64,7 @@ def test_pass_operator_matches_exact_oracle(dilute):
         scale = np.abs(ref).max()
         out = ctx.apply_operator(vec, mfs.MIXED_PASS)
         assert np.abs(out - ref).max() <= 1e-5 * scale
-    # control: every sphere near (no far field) -> the all-pairs pass operator exactly
+    # control: every sphere near (no far field) -> the all-pairs pass operator
     with mfs.Context(0) as c2:
         c2.set_spheres(centres)
         c2.build(**KW, **dict(FAR, far_dist=1e3))
@@ -73,7 +75,7 @@ def test_pass_operator_matches_exact_oracle(dilute):
             for vec in (mu, _krylov_like(op, mu)):
                 a = c2.apply_operator(vec, mfs.MIXED_PASS)
                 b = c3.apply_operator(vec, mfs.MIXED_PASS)
-                assert np.array_equal(a, b)
+                assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
                 assert np.abs(a - op.apply(vec)).max() <= 1e-7 * np.abs(a).max()
 
 
