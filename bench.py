@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--kernel-case", type=int, default=0,
                     help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
     ap.add_argument("--profile-case", default="", choices=["", "far", "tensor"],
-                    help="profiling case: 'far' = pass-operator applies on a 24-sphere suspension with the far field, "
+                    help="profiling case: 'far' = pass-operator applies on a 343-sphere lattice with the far field, "
                          "'tensor' = the same on 60 contact-free spheres with the tensor-core step 1; then exit")
     ap.add_argument("--suspension", type=int, default=200,
                     help="spheres of the far-field suspension solve among the extras (0 = skip)")
@@ -262,6 +262,10 @@ def suspension_solve(device, P=200, tol=SWEEP_TOL):
     ctx.build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC, **FAR)
     setup = time.perf_counter() - t0
     s = ctx.sizes()
+    t0 = time.perf_counter()
+    sh = ctx.tune_pairs()
+    tune_s = time.perf_counter() - t0
+    shapes = {f: getattr(sh, f) for f, _ in sh._fields_}
     v, w = workloads.rigid_velocities(P, seed=1)
     ctx.set_rigid_velocities(v, w)
     ctx.set_profiling(True)
@@ -287,7 +291,7 @@ def suspension_solve(device, P=200, tol=SWEEP_TOL):
     out = {"spheres": P, "contacts": s.n_contacts, "nodes": s.n_colloc, "setup_s": setup,
            "pairs_exact_per_apply": s.pairs_fp, "pairs_near_per_apply": s.pairs_near_fp,
            "equivalent_pairs_per_apply": s.pairs_far_eq, "device_GB": ctx.memory_in_use() / 1e9,
-           "applies_ms": applies, "solve_s": solve_s, "iters": info.iters, "refinements": info.refinements,
+           "tuned_shapes": shapes, "tune_s": tune_s, "applies_ms": applies, "solve_s": solve_s, "iters": info.iters, "refinements": info.refinements,
            "rel_residual_exact_operator": info.rel_residual, "converged": info.converged, "tol": tol,
            "near_pairs_per_s": t.pair_interactions / (t.pair_ms / 1000.0) if t.pair_ms else None,
            "equivalent_pairs_per_s": t.far_pairs / (t.far_ms / 1000.0) if t.far_ms else None,
@@ -339,12 +343,19 @@ def cluster_example(device, P=100, delta=1e-2, r_proxy=0.75, far=False):
     x = np.concatenate([centres[k] + chk for k in ks])
     u = ctx.eval_velocity(x)
     ubc = -(U[None, :] + x @ E.T + np.cross(Om[None, :], x))
-    eres = float((np.linalg.norm(u - ubc, axis=1) / np.linalg.norm(ubc, axis=1)).max())
+    # pointwise ratio where |u_bc| is at least 1e-2 of its largest value on the sphere (the shear
+    # flow vanishes on the plane y = 0, through the cluster); the plain maximum is reported too
+    nb = np.linalg.norm(ubc, axis=1).reshape(len(ks), -1)
+    err = np.linalg.norm(u - ubc, axis=1).reshape(len(ks), -1)
+    keep = nb >= 1e-2 * nb.max(axis=1, keepdims=True)
+    eres = float((err[keep] / nb[keep]).max())
+    eres_all = float((err / nb).max())
     lam = ctx.strengths()
     s = ctx.sizes()
     out = {"spheres": P, "delta": delta, "r_proxy": r_proxy, "far_field": far, "setup_s": setup,
            "solve_s": e0.elapsed_time(e1) / 1000.0, "iters": info.iters, "converged": info.converged,
-           "rel_residual": info.rel_residual, "eps_res_max_sampled": eres, "spheres_checked": int(len(ks)),
+           "rel_residual": info.rel_residual, "eps_res_max_sampled": eres, "eps_res_max_sampled_all_points": eres_all,
+           "spheres_checked": int(len(ks)),
            "lambda_max": float(np.abs(lam).max()), "dof": 3 * s.n_colloc, "factors": s.n_factors,
            "near_ms": t.pair_ms, "far_ms": t.far_ms, "gemv_ms": t.gemv_ms,
            "paper_P100_iters": {"1e-2,0.75": 92, "1e-3,0.75": 122, "1e-3,0.65": 116},
@@ -359,9 +370,12 @@ def profile_case(kind, device):
     from paper_2407_03343_gb300 import mfs, workloads
     ctx = mfs.Context(device)
     if kind == "far":
-        # 24 spheres at volume fraction 0.08, N = 400, M0 = 800: a few GB on the device
-        ctx.set_spheres(workloads.suspension(24, 0.08, seed=3))
-        ctx.build(n_proxy=400, r_proxy=R_PROXY, m_basic=800, **FAR)
+        # 343 spheres on a 7 x 7 x 7 lattice 3 radii apart (no contacts: one shared factor, little
+        # device memory), 480 nodes each: 343 tiles of 512 nodes, 4 per thread, as in the
+        # 200-sphere suspension; 6 near neighbours, 336 far spheres
+        g = np.arange(7) * 3.0
+        ctx.set_spheres(np.array([[x, y, z] for x in g for y in g for z in g]))
+        ctx.build(n_proxy=160, r_proxy=R_PROXY, m_basic=480, **FAR)
     else:
         g = np.arange(4) * 3.0
         c = np.array([[x, y, z] for x in g for y in g for z in g])[:60]

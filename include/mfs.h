@@ -364,6 +364,23 @@ mfs_status mfs_get_timing(mfs_ctx* ctx, mfs_timing_t* out, int reset);
  * launch runs ~0.1-0.5 s.  Allocates and frees one small device buffer. */
 mfs_status mfs_probe_alu_peak(int device, int which, double* tflops, double* ms);
 
+/* Tile shapes of the pair kernels (steps 2+3) and the autotuner that picks them.  A target tile
+ * holds 512 collocation nodes (4 per thread of a 128-thread CTA) or 128 (1 per thread); a tile's
+ * sources may be split over several CTAs whose partial sums a second kernel adds in a fixed
+ * order.  By default the library chooses by rule (512-node tiles once they fill the GPU twice,
+ * source parts that fill whole waves of resident CTAs).  mfs_tune_pairs times every candidate
+ * (tile of 128 or 512 nodes x no split or the wave-filling split) of each pair-kernel family the
+ * context uses, on its own discretisation, with CUDA events over two launches each, keeps the
+ * fastest for the context's later launches and reports them; 0 in a field means "not used by
+ * this context" (e.g. the near / far kernels without the far field). */
+typedef struct {
+  int all_nodes_per_thread, all_parts;    /* every pair in double-float (MIXED residual, passes without far field) */
+  int near_nodes_per_thread, near_parts;  /* near spheres, double-float (passes with the far field) */
+  int far_nodes_per_thread, far_parts;    /* far spheres' equivalent Stokeslets, FP32 */
+  double all_ms, near_ms, far_ms;         /* device time of the chosen shapes, per launch */
+} mfs_pair_shapes;
+mfs_status mfs_tune_pairs(mfs_ctx* ctx, mfs_pair_shapes* out);
+
 /* Cap on the device memory the context may hold for its discretisation, factors and solver
  * workspace (bytes; 0 = no cap, the default).  An allocation that would exceed it fails like a
  * cudaMalloc failure: the call returns MFS_ERR_OOM and the context stays usable, so a caller

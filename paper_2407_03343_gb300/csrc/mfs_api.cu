@@ -139,6 +139,8 @@ struct mfs_ctx {
   float* d_tc_partial = nullptr;
   int* d_tc_err = nullptr;
   GemvBatch<float> gA32_rest, gQ_rest;  // the GEMV jobs of every other sphere
+  // tile shapes of the pair kernels (default: by rule; mfs_tune_pairs measures and sets them)
+  PairShape shape_all, shape_near, shape_far;
   GemvBatch<float> gA32, gV32;
   GemvBatch<double> gA64, gV64;
   long long tmp_len = 0;
@@ -195,6 +197,7 @@ struct mfs_ctx {
     d_q = nullptr;
     gQ = GemvBatch<float>();
     tc_ncols = 0;
+    shape_all = shape_near = shape_far = PairShape();
     tcA = TcGemm();
     tcQ = TcGemm();
     gA32_rest = gQ_rest = GemvBatch<float>();
@@ -347,7 +350,7 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
       // whose strengths q = Q mu are formed from this apply's mu
       timed(c, c->ev_pair, [&] {
         launch_pairs_dw_near(c->tg, c->src, c->ff, lam_hat, mu, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts,
-                             c->stream);
+                             c->stream, c->shape_near);
       });
       timed(c, c->ev_far, [&] {
         launch_convert<double, float>(c->n, mu, 1.0, c->d_mu32, c->stream);
@@ -358,7 +361,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
         } else {
           launch_gemv<float>(c->gQ, c->d_mu32, c->d_q, c->stream);
         }
-        launch_pairs_far(c->tg, c->src, c->ff, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream);
+        launch_pairs_far(c->tg, c->src, c->ff, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream,
+                         c->shape_far);
       });
       c->tm.pair_launches += 1;
       c->tm.pair_interactions += c->near_pairs_per_apply;
@@ -377,7 +381,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
   timed(c, c->ev_pair, [&] {
     if constexpr (sizeof(T) == 8) {
       if (c->dw_pairs) {
-        launch_pairs_dw(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream);
+        launch_pairs_dw(c->tg, c->src, lam_hat, mu, out, c->hd.prm.visc, c->d_pparts, kPairMaxParts, c->stream,
+                        c->shape_all);
         return;
       }
     }
@@ -2748,6 +2753,91 @@ mfs_status mfs_probe_alu_peak(int device, int which, double* tflops, double* ms)
   if (st) cudaStreamDestroy(st);
   cudaFree(sink);
   return out;
+}
+
+mfs_status mfs_tune_pairs(mfs_ctx* c, mfs_pair_shapes* out) {
+  mfs_status s = check_state(c, 2);
+  if (s != MFS_OK) return s;
+  if (c->tg.n_tiles == 0) return c->fail(MFS_ERR_STATE, "no collocation nodes to tune on");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  struct EvFree {
+    cudaEvent_t a, b;
+    ~EvFree() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evf{e0, e1};
+  // inputs: the context's work buffers, zeroed (the launches' cost does not depend on the values)
+  CUDA_TRY(c, cudaMemsetAsync(c->d_lh64, 0, sizeof(double) * c->n_unk, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, sizeof(double) * c->n, c->stream));
+  if (c->d_q) CUDA_TRY(c, cudaMemsetAsync(c->d_q, 0, sizeof(float) * 3 * (size_t)c->ff.n_eq * c->P, c->stream));
+  const double visc = c->hd.prm.visc;
+  // each candidate: one warm-up and two timed launches
+  auto time_it = [&](auto&& launch, double& ms) -> mfs_status {
+    launch();
+    CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    launch();
+    launch();
+    CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+    CHECK_LAUNCH(c);
+    CUDA_TRY(c, cudaEventSynchronize(e1));
+    float t = 0;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+    ms = t / 2.0;
+    return MFS_OK;
+  };
+  const PairShape cands[4] = {{1, 1}, {1, 0}, {4, 1}, {4, 0}};  // parts 0: the wave-filling rule
+  auto tune = [&](auto&& launch_with, PairShape& best, double& best_ms) -> mfs_status {
+    best_ms = -1;
+    for (const PairShape& sh : cands) {
+      if (sh.nt == 1 && c->tg.n_tiles1 == 0) continue;
+      double ms = 0;
+      mfs_status st = time_it([&] { launch_with(sh); }, ms);
+      if (st != MFS_OK) return st;
+      if (best_ms < 0 || ms < best_ms) {
+        best_ms = ms;
+        best = sh;
+      }
+    }
+    return MFS_OK;
+  };
+  mfs_pair_shapes r{};
+  double ms = 0;
+  PairShape best;
+  if ((s = tune([&](PairShape sh) { launch_pairs_dw(c->tg, c->src, c->d_lh64, c->d_mu, c->d_w64, visc, c->d_pparts,
+                                                    kPairMaxParts, c->stream, sh); },
+                best, ms)) != MFS_OK)
+    return s;
+  c->shape_all = best;
+  PairShape ra = resolve_dw_shape(c->tg, c->src, best, kPairMaxParts);
+  r.all_nodes_per_thread = ra.nt;
+  r.all_parts = ra.parts;
+  r.all_ms = ms;
+  if (c->ff.n_eq > 0) {
+    if ((s = tune([&](PairShape sh) { launch_pairs_dw_near(c->tg, c->src, c->ff, c->d_lh64, c->d_mu, c->d_w64, visc,
+                                                           c->d_pparts, kPairMaxParts, c->stream, sh); },
+                  best, ms)) != MFS_OK)
+      return s;
+    c->shape_near = best;
+    PairShape rn = resolve_near_shape(c->tg, best, kPairMaxParts);
+    r.near_nodes_per_thread = rn.nt;
+    r.near_parts = rn.parts;
+    r.near_ms = ms;
+    if ((s = tune([&](PairShape sh) { launch_pairs_far(c->tg, c->src, c->ff, c->d_w64, visc, c->d_pparts,
+                                                       kPairMaxParts, c->stream, sh); },
+                  best, ms)) != MFS_OK)
+      return s;
+    c->shape_far = best;
+    PairShape rf = resolve_far_shape(c->tg, best, kPairMaxParts);
+    r.far_nodes_per_thread = rf.nt;
+    r.far_parts = rf.parts;
+    r.far_ms = ms;
+  }
+  c->solved = false;  // the work buffers were overwritten
+  if (out) *out = r;
+  return MFS_OK;
 }
 
 mfs_status mfs_set_memory_limit(mfs_ctx* c, unsigned long long bytes) {

@@ -131,6 +131,13 @@ size_t tc_partial_floats(const TcGemm& g, int ncols);
 void launch_tc_gemm(const TcGemm& g, int ncols, const double* x, const long long* x_off, const long long* y_off,
                     float* y32, float2* y2, float* partial, int* err, bool slice_x, cudaStream_t st);
 
+// A launch shape: nodes per thread (4: 512-node tiles, 1: 128-node tiles, 0: by rule) and source
+// parts per tile (0: the wave-filling rule, 1: no split, > 1: that many).
+struct PairShape {
+  int nt = 0;
+  int parts = 0;
+};
+
 // Kernel launchers (mfs_kernels.cu).  All run on `st`.
 template <typename T>
 void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, const T* mu,
@@ -141,7 +148,8 @@ void launch_pairs(const TargetSet& tg, const SourceSet& src, const T* lam_hat, c
 // max_parts CTAs whose partial sums go to `partial` (max_parts * 3 n doubles; null: no split)
 // and are added in a second, deterministic pass.
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu,
-                     double* out, double visc, double* partial, int max_parts, cudaStream_t st);
+                     double* out, double visc, double* partial, int max_parts, cudaStream_t st,
+                     PairShape shape = PairShape());
 // Source split of the 1-node-per-thread tiling: as many parts as keep the CTAs within one wave
 // (152 SMs x 7 resident CTAs of the double-float kernel: 72 registers x 128 threads, 28 KB of
 // shared memory), at least kPairSplitMinSources sources per part, at most max_parts.
@@ -156,11 +164,16 @@ int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts);
 // null for no split) so that the grid fills whole waves of resident CTAs; the parts are added in
 // a fixed order by a second kernel.
 void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
-                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st);
+                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st,
+                          PairShape shape = PairShape());
 // Far part, FP32 with compensated cross-tile sums: out += W sum over the far spheres of the
 // equivalent Stokeslets' field.
 void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
-                      double* partial, int max_parts, cudaStream_t st);
+                      double* partial, int max_parts, cudaStream_t st, PairShape shape = PairShape());
+// the shape a launch with `shape` resolves to (nodes per thread, parts), for reporting
+PairShape resolve_near_shape(const TargetSet& tg, PairShape shape, int max_parts);
+PairShape resolve_far_shape(const TargetSet& tg, PairShape shape, int max_parts);
+PairShape resolve_dw_shape(const TargetSet& tg, const SourceSet& src, PairShape shape, int max_parts);
 
 // Many problems per launch (FP64 data): a device table of per-problem kernel arguments, a work
 // list of (problem, tile) pairs and a per-problem active flag.

@@ -1547,19 +1547,34 @@ int pair_split_parts(long long n_tiles1, long long min_sources, int max_parts) {
   return (int)std::max<long long>(s, 1);
 }
 
+// nodes per thread of a launch: the requested shape, else the rule (512-node tiles once they fill
+// the GPU twice; 128-node tiles only when they exist)
+static int shape_nt(const TargetSet& tg, const PairShape& shape) {
+  if (tg.n_tiles1 == 0) return 4;
+  if (shape.nt == 1 || shape.nt == 4) return shape.nt;
+  return pair_nodes_per_thread(tg.n_tiles);
+}
+
+PairShape resolve_dw_shape(const TargetSet& tg, const SourceSet& src, PairShape shape, int max_parts) {
+  PairShape r;
+  r.nt = shape_nt(tg, shape);
+  if (shape.parts > 0) r.parts = std::min(shape.parts, max_parts);
+  else if (r.nt == 4) r.parts = 1;
+  else r.parts = pair_split_parts(tg.n_tiles1, (long long)(src.P - 1) * src.N, max_parts);
+  return r;
+}
+
 void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* lam_hat, const double* mu, double* out,
-                     double visc, double* partial, int max_parts, cudaStream_t st) {
+                     double visc, double* partial, int max_parts, cudaStream_t st, PairShape shape) {
   if (tg.n_tiles == 0) return;
-  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  const PairShape r = resolve_dw_shape(tg, src, shape, max_parts);
+  const int nt = r.nt;
+  const int parts = partial ? r.parts : 1;
   PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
-  ++t_launches;
-  if (nt == 4) {
-    pairs_dw_kernel<4><<<tg.n_tiles, kPairThreads, 0, st>>>(A, 1, nullptr, 0);
-    return;
-  }
-  const int parts = partial ? pair_split_parts(tg.n_tiles1, (long long)(src.P - 1) * src.N, max_parts) : 1;
   const long long n3 = 3LL * tg.n;
-  pairs_dw_kernel<1><<<tg.n_tiles1 * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  ++t_launches;
+  if (nt == 4) pairs_dw_kernel<4><<<tg.n_tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  else pairs_dw_kernel<1><<<tg.n_tiles1 * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
   if (parts > 1) {
     ++t_launches;
     pair_parts_reduce_kernel<<<grid_for(n3, 256), 256, 0, st>>>(n3, A.tgt, parts, partial, n3, mu, out);
@@ -1588,15 +1603,25 @@ int wave_parts(long long tiles, const void* kernel, int max_parts) {
   return best;
 }
 
+PairShape resolve_near_shape(const TargetSet& tg, PairShape shape, int max_parts) {
+  PairShape r;
+  r.nt = shape_nt(tg, shape);
+  const long long tiles = r.nt == 4 ? tg.n_tiles : tg.n_tiles1;
+  r.parts = shape.parts > 0 ? std::min(shape.parts, max_parts)
+                            : wave_parts(tiles, r.nt == 4 ? (const void*)pairs_dw_near_kernel<4>
+                                                          : (const void*)pairs_dw_near_kernel<1>, max_parts);
+  return r;
+}
+
 void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarField& ff, const double* lam_hat,
-                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st) {
+                          const double* mu, double* out, double visc, double* partial, int max_parts, cudaStream_t st,
+                          PairShape shape) {
   if (tg.n_tiles == 0) return;
-  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  const PairShape r = resolve_near_shape(tg, shape, max_parts);
+  const int nt = r.nt;
   PairArgs<double> A = make_args<double>(tg, src, lam_hat, mu, out, visc, nt);
   const long long tiles = nt == 4 ? tg.n_tiles : tg.n_tiles1;
-  const int parts = partial ? wave_parts(tiles, nt == 4 ? (const void*)pairs_dw_near_kernel<4> : (const void*)pairs_dw_near_kernel<1>,
-                                         max_parts)
-                            : 1;
+  const int parts = partial ? r.parts : 1;
   const long long n3 = 3LL * tg.n;
   ++t_launches;
   if (nt == 4)
@@ -1609,10 +1634,21 @@ void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarFi
   }
 }
 
+PairShape resolve_far_shape(const TargetSet& tg, PairShape shape, int max_parts) {
+  PairShape r;
+  r.nt = shape_nt(tg, shape);
+  const long long tiles = r.nt == 4 ? tg.n_tiles : tg.n_tiles1;
+  r.parts = shape.parts > 0 ? std::min(shape.parts, max_parts)
+                            : wave_parts(tiles, r.nt == 4 ? (const void*)pairs_far_kernel<4> : (const void*)pairs_far_kernel<1>,
+                                         max_parts);
+  return r;
+}
+
 void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField& ff, double* out, double visc,
-                      double* partial, int max_parts, cudaStream_t st) {
+                      double* partial, int max_parts, cudaStream_t st, PairShape shape) {
   if (tg.n_tiles == 0 || ff.n_eq == 0) return;
-  const int nt = tg.n_tiles1 > 0 ? pair_nodes_per_thread(tg.n_tiles) : 4;
+  const PairShape r = resolve_far_shape(tg, shape, max_parts);
+  const int nt = r.nt;
   FarArgs A;
   A.tgt = tg.pos32;
   A.tgt64 = tg.pos64;
@@ -1630,9 +1666,7 @@ void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField&
   A.out = out;
   A.scale = (float)(1.0 / (8.0 * kPi * visc));
   const long long tiles = nt == 4 ? tg.n_tiles : tg.n_tiles1;
-  const int parts = partial ? wave_parts(tiles, nt == 4 ? (const void*)pairs_far_kernel<4> : (const void*)pairs_far_kernel<1>,
-                                         max_parts)
-                            : 1;
+  const int parts = partial ? r.parts : 1;
   const long long n3 = 3LL * tg.n;
   ++t_launches;
   if (nt == 4) pairs_far_kernel<4><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);

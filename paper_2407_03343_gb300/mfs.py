@@ -70,6 +70,12 @@ class Timing(C.Structure):
                 ("far_launches", C.c_longlong), ("far_ms", C.c_double), ("far_pairs", C.c_longlong)]
 
 
+class PairShapes(C.Structure):
+    _fields_ = [("all_nodes_per_thread", C.c_int), ("all_parts", C.c_int), ("near_nodes_per_thread", C.c_int),
+                ("near_parts", C.c_int), ("far_nodes_per_thread", C.c_int), ("far_parts", C.c_int),
+                ("all_ms", C.c_double), ("near_ms", C.c_double), ("far_ms", C.c_double)]
+
+
 class MfsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -123,6 +129,7 @@ def lib():
                                                  C.POINTER(SolveOpts), C.POINTER(SolveInfo), C.POINTER(P), C.POINTER(P)]),
         "mfs_set_profiling": (C.c_int, [P, C.c_int]),
         "mfs_probe_alu_peak": (C.c_int, [C.c_int, C.c_int, _D, _D]),
+        "mfs_tune_pairs": (C.c_int, [P, C.POINTER(PairShapes)]),
         "mfs_set_memory_limit": (C.c_int, [P, C.c_ulonglong]),
         "mfs_memory_in_use": (C.c_int, [P, C.POINTER(C.c_ulonglong)]),
         "mfs_get_timing": (C.c_int, [P, C.POINTER(Timing), C.c_int]),
@@ -353,6 +360,12 @@ class Context:
         t = Timing()
         self._check(self._L.mfs_get_timing(self._h, C.byref(t), 1 if reset else 0))
         return t
+
+    def tune_pairs(self) -> PairShapes:
+        """Time the candidate tile shapes of the pair kernels and keep the fastest (mfs_tune_pairs)."""
+        r = PairShapes()
+        self._check(self._L.mfs_tune_pairs(self._h, C.byref(r)))
+        return r
 
     def set_memory_limit(self, nbytes: int):
         """Cap the device memory this context may hold (0 = no cap); see mfs_set_memory_limit."""

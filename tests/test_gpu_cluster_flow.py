@@ -10,11 +10,14 @@ Checked:
   * a 10-sphere cluster in each flow against the oracle's O3 solve: forces/torques to 1e-5,
     velocity at the check points to 1e-3;
   * the paper's P = 100 settings of Table cluster_table (N = 686 proxies, GMRES tolerance 1e-6):
-    the solve converges in a number of iterations of the size the table prints (92, 122, 116;
-    the Fibonacci grids that stand in for the spherical designs change the count, so only the
-    size is compared: within a factor of three), the largest relative surface residual at the
-    check points (eq. residual) meets the paper's 1e-3 target, and the strengths stay
-    moderate (the table prints max |lambda| of 9.8 and 9.5 for R_p = 0.75 and 316 for 0.65).
+    the solve converges in a number of iterations close to the table's 92, 122, 116 (within 30 %;
+    the Fibonacci grids that stand in for the spherical designs change the count slightly;
+    measured 93 / 111 / 108); the surface residual (eq. residual) relative to each sphere's
+    largest boundary speed stays at the table's ~1e-4 level (below 1e-3; measured 1e-4..2.2e-4),
+    and pointwise, where the shear flow's boundary data is not near its zero plane, below 1e-2
+    (measured 2e-3..5e-3: the Fibonacci grids are coarser than the designs); the strengths stay
+    moderate (the table prints max |lambda| of 9.8 and 9.5 for R_p = 0.75 and 316 for 0.65;
+    measured 7.9 / 8.1 / 167).
 """
 import numpy as np
 import pytest
@@ -57,12 +60,21 @@ def test_small_cluster_in_flow_matches_oracle(kind):
         assert np.abs(ctx.eval_velocity(x) - uo).max() <= 1e-3 * np.abs(uo).max()
 
 
-def _surface_residual(ctx, d, U, E, Om):
-    """eq. residual: max over the check points of |u - u_bc| / |u_bc|, u_bc = -u_inf."""
-    x = np.concatenate(d.check)
-    u = ctx.eval_velocity(x)
-    ubc = -(U[None, :] + x @ E.T + np.cross(Om[None, :], x))
-    return float((np.linalg.norm(u - ubc, axis=1) / np.linalg.norm(ubc, axis=1)).max())
+def _surface_residuals(ctx, d, U, E, Om):
+    """eq. residual at the check points, u_bc = -u_inf: (a) the pointwise ratio |u - u_bc| / |u_bc|
+    where |u_bc| is at least 1e-2 of its largest value on that sphere (the shear flow vanishes on
+    the plane y = 0, which runs through the cluster; there the pointwise ratio has no meaning),
+    (b) |u - u_bc| relative to the largest |u_bc| on that sphere; the largest of each."""
+    pw = rel = 0.0
+    for x in d.check:
+        u = ctx.eval_velocity(x)
+        ubc = -(U[None, :] + x @ E.T + np.cross(Om[None, :], x))
+        nb = np.linalg.norm(ubc, axis=1)
+        err = np.linalg.norm(u - ubc, axis=1)
+        keep = nb >= 1e-2 * nb.max()
+        pw = max(pw, float((err[keep] / nb[keep]).max()))
+        rel = max(rel, float(err.max() / nb.max()))
+    return pw, rel
 
 
 @pytest.mark.parametrize("delta,r_p,printed_iters", [(1e-2, 0.75, 92), (1e-3, 0.75, 122), (1e-3, 0.65, 116)])
@@ -78,9 +90,14 @@ def test_cluster_table_settings(delta, r_p, printed_iters):
         ctx.set_rigid_velocities(np.zeros((100, 3)), np.zeros((100, 3)))
         info = ctx.solve(precision="mixed", tol=1e-6)
         assert info.converged == 1
-        assert printed_iters / 3 <= info.iters <= 3 * printed_iters, info.iters
+        # measured: 93 / 111 / 108 against the printed 92 / 122 / 116
+        assert 0.7 * printed_iters <= info.iters <= 1.3 * printed_iters, info.iters
         d = geometry.build(centres, 1.0, geometry.Params(**kw))
-        assert _surface_residual(ctx, d, U, E, Om) <= 1e-3
+        pw, rel = _surface_residuals(ctx, d, U, E, Om)
+        # measured: pointwise 2e-3..5e-3, relative to the sphere's largest boundary speed 1e-4..2.2e-4
+        # (the table prints 6.9e-5..1.1e-4)
+        assert pw <= 1e-2 and rel <= 1e-3, (pw, rel)
         lam = lib_to_oracle(d, ctx.strengths())
         lam_max = max(np.abs(x).max() for x in lam)
-        assert lam_max <= (100.0 if r_p > 0.7 else 3000.0)
+        # measured: 7.9 / 8.1 / 167 against the printed 9.8 / 9.5 / 316
+        assert lam_max <= (20.0 if r_p > 0.7 else 1000.0), lam_max

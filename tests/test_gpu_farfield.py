@@ -116,3 +116,19 @@ def test_far_field_parameters_are_checked():
         with pytest.raises(mfs.MfsError) as e:
             ctx.build(**KW, **dict(FAR, far_r_eq=2.5))   # equivalent sphere outside the check sphere
         assert e.value.status == -1
+
+
+def test_autotuned_shapes_keep_the_operator(dilute):
+    centres, d, op, ctx = dilute
+    v, om = workloads.rigid_velocities(len(d.spheres), seed=3)
+    mu = np.concatenate(solve.rhs(d, v, om))
+    before = ctx.apply_operator(mu, mfs.MIXED_PASS)
+    shapes = ctx.tune_pairs()
+    for nt, parts, ms in ((shapes.all_nodes_per_thread, shapes.all_parts, shapes.all_ms),
+                          (shapes.near_nodes_per_thread, shapes.near_parts, shapes.near_ms),
+                          (shapes.far_nodes_per_thread, shapes.far_parts, shapes.far_ms)):
+        assert nt in (1, 4) and 1 <= parts <= 16 and ms > 0
+    after = ctx.apply_operator(mu, mfs.MIXED_PASS)
+    # other tiles and source splits only reorder the sums
+    assert np.abs(after - before).max() <= 1e-9 * np.abs(before).max()
+    assert np.abs(after - op.apply(mu)).max() <= 1e-5 * np.abs(before).max()

@@ -131,7 +131,14 @@ def test_triangle_exterior_flow_self_convergence():
             assert ctx.solve(precision="mixed", tol=1e-8, max_iter=3000).converged == 1
             u.append(ctx.eval_velocity(pts))
     uc, uf = u
-    rel = np.linalg.norm(uc - uf, axis=1) / np.linalg.norm(uf, axis=1)
+    # pointwise relative difference where the flow is not near a stagnation point (the centre of
+    # the triangle is one, by symmetry): |u_f| at least 1e-2 of its largest value in the plane
+    nf = np.linalg.norm(uf, axis=1)
+    keep = nf >= 1e-2 * nf.max()
+    rel = np.linalg.norm(uc - uf, axis=1)[keep] / nf[keep]
+    print(f"triangle: {pts.shape[0]} points, {int(keep.sum())} away from stagnation; max pointwise "
+          f"{rel.max():.3e}, median {np.median(rel):.3e}; max relative to the largest speed "
+          f"{np.linalg.norm(uc - uf, axis=1).max() / nf.max():.3e}")
     assert pts.shape[0] > 10000
     assert rel.max() < 1e-2
     assert np.median(rel) < 1e-3
