@@ -197,9 +197,10 @@ mfs_status mfs_set_rigid_velocities_device(mfs_ctx* ctx, const double* d_v, cons
  * with s_F = 1/(6 pi visc a) and s_T = 1/(8 pi visc a^3) (the single-sphere drag and torque
  * coefficients, which bring the border rows to the scale of the velocities).  Host arrays,
  * copied before return; non-finite values give MFS_ERR_ARG.  Requires mfs_build.  The mobility
- * problem is solved with MFS_FP64 or MFS_MIXED (MFS_FP32 and the batched solves give
- * MFS_ERR_UNSUPPORTED).  A later mfs_set_rigid_velocities* returns the context to the
- * resistance problem. */
+ * problem is solved with MFS_FP64 or MFS_MIXED, singly or in mfs_batch_solve together with
+ * resistance problems (MFS_FP32 gives MFS_ERR_UNSUPPORTED; mfs_batch_solve_rhs*, which brings
+ * rigid velocities, solves every problem as a resistance problem).  A later
+ * mfs_set_rigid_velocities* returns the context to the resistance problem. */
 mfs_status mfs_set_forces_torques(mfs_ctx* ctx, const double* F, const double* T);
 /* Rigid velocities V (P*3) and Omega (P*3) of the last mobility solve, host arrays;
  * MFS_ERR_STATE before one. */
@@ -289,7 +290,8 @@ mfs_status mfs_apply_pairs(mfs_ctx* ctx, int precision, const double* lambda_hat
 mfs_status mfs_apply_precond_noalloc(mfs_ctx* ctx, const double* d_mu, double* d_lambda_hat);
 
 /* ---- many independent problems ----
- * Solves every context (each already built and given boundary data) with the same options,
+ * Solves every context (each already built and given boundary data: rigid velocities, or
+ * prescribed forces and torques for a mobility problem) with the same options,
  * all at once: one GMRES runs in lockstep over the concatenation of the problems, each with
  * its own Krylov coefficients, Hessenberg matrix and convergence test, and every kernel
  * launch (pseudo-inverse GEMVs, pair sums, Gram-Schmidt) covers all problems still iterating.
@@ -369,7 +371,8 @@ mfs_status mfs_probe_alu_peak(int device, int which, double* tflops, double* ms)
  * sources may be split over several CTAs whose partial sums a second kernel adds in a fixed
  * order.  By default the library chooses by rule (512-node tiles once they fill the GPU twice,
  * source parts that fill whole waves of resident CTAs).  mfs_tune_pairs times every candidate
- * (tile of 128 or 512 nodes x no split or the wave-filling split) of each pair-kernel family the
+ * (tile of 128 or 512 nodes x no split or the wave-filling split; for the far kernel with 512-node
+ * tiles also scalar or packed two-lane FP32 instructions) of each pair-kernel family the
  * context uses, on its own discretisation, with CUDA events over two launches each, keeps the
  * fastest for the context's later launches and reports them; 0 in a field means "not used by
  * this context" (e.g. the near / far kernels without the far field). */
@@ -377,6 +380,7 @@ typedef struct {
   int all_nodes_per_thread, all_parts;    /* every pair in double-float (MIXED residual, passes without far field) */
   int near_nodes_per_thread, near_parts;  /* near spheres, double-float (passes with the far field) */
   int far_nodes_per_thread, far_parts;    /* far spheres' equivalent Stokeslets, FP32 */
+  int far_packed;                         /* 1: the far kernel issues packed FP32 pairs (f32x2) */
   double all_ms, near_ms, far_ms;         /* device time of the chosen shapes, per launch */
 } mfs_pair_shapes;
 mfs_status mfs_tune_pairs(mfs_ctx* ctx, mfs_pair_shapes* out);

@@ -594,6 +594,9 @@ mfs_status check_state(mfs_ctx* c, int need) {
 struct BatchPlan {
   std::vector<mfs_ctx*> key;
   std::vector<long long> key_build;
+  std::vector<int> mob;            // per problem: 1 = mobility (6P border unknowns after the node rows)
+  std::vector<long long> nlen;     // node rows 3 n_colloc per problem
+  long long* d_nlen = nullptr;
   int K = 0, nt = 1;
   long long n_total = 0, u_total = 0, t_total = 0;
   std::vector<long long> voff, uoff, toff;
@@ -669,11 +672,12 @@ bool put(BatchPlan* B, T*& dst, const std::vector<T>& v) {
 }
 
 // Builds the concatenated layout, the pair work list, the GEMV job tables and the vector chunks.
-mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) {
+mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector<int>& mob, BatchPlan*& out) {
   BatchPlan* B = new (std::nothrow) BatchPlan();
   if (!B) return c0->fail(MFS_ERR_OOM, "host allocation failed: batch plan");
   B->K = K;
   B->key.assign(ctxs, ctxs + K);
+  B->mob = mob;
   for (int p = 0; p < K; ++p) B->key_build.push_back(ctxs[p]->build_id);
   B->voff.assign(K + 1, 0);
   B->uoff.assign(K + 1, 0);
@@ -681,7 +685,8 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
   long long tiles_large = 0;
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
-    B->voff[p + 1] = B->voff[p] + c->n;
+    B->nlen.push_back(c->n);
+    B->voff[p + 1] = B->voff[p] + c->n + (mob[p] ? 6LL * c->P : 0);
     B->uoff[p + 1] = B->uoff[p] + c->n_unk;
     B->toff[p + 1] = B->toff[p] + c->tmp_len;
     B->pairs_p.push_back(c->pairs_per_apply);
@@ -718,7 +723,7 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, BatchPlan*& out) 
             cudaMemcpy(B->d_args, args4.data(), args4.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(B->d_args1, args1.data(), args1.size(), cudaMemcpyHostToDevice) == cudaSuccess;
   ok = ok && put(B, B->d_work, work4) && put(B, B->d_work1, work1) && put(B, B->d_uoff, B->uoff) &&
-       put(B, B->d_voff, B->voff);
+       put(B, B->d_voff, B->voff) && put(B, B->d_nlen, B->nlen);
   B->d_active = B->alloc<int>(K);
   B->d_cwork = B->alloc<int2>(work4.size());
   B->d_cwork1 = B->alloc<int2>(work1.size());
@@ -926,8 +931,19 @@ void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
                            B->d_voff, 1, nullptr, 0, B->seg, R.st);
     else
       launch_pairs_batch64(R.dw, B->d_args1, B->d_cwork1, B->n_cwork1, B->d_active, 1, B->lh, in, out, B->d_uoff,
-                           B->d_voff, parts, B->pparts, B->n_total, B->seg, R.st);
+                           B->d_voff, parts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen);
   });
+  // mobility problems: the rigid motion of the border unknowns, and their force/torque rows
+  // (the bordered operator of the single solves, problem by problem)
+  for (int p = 0; p < B->K; ++p)
+    if (B->mob[p] && R.act[p]) {
+      mfs_ctx* cp = B->key[p];
+      const double a = cp->a, mu = cp->hd.prm.visc;
+      launch_rigid_sub(cp->tg.n, cp->d_owner, cp->tg.pos64, in + B->voff[p] + B->nlen[p], out + B->voff[p], R.st);
+      launch_forces_torques_scaled(cp->src, B->lh + B->uoff[p], out + B->voff[p] + B->nlen[p],
+                                   out + B->voff[p] + B->nlen[p] + 3, 6, 1.0 / (6.0 * kPi * mu * a),
+                                   1.0 / (8.0 * kPi * mu * a * a * a), R.st);
+    }
   c->tm.gemv_launches += 2;
   c->tm.pair_launches += 1;
   c->tm.pair_kind = R.dw ? MFS_MIXED : MFS_FP64;
@@ -1187,7 +1203,8 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     mfs_status s = check_state(ctxs[p], 2);
     if (s != MFS_OK) return s;
     if (!ctxs[p]->factored) return ctxs[p]->fail(MFS_ERR_STATE, "built without one-body factors (build_factors = 0)");
-    if (ctxs[p]->mode != 0) return ctxs[p]->fail(MFS_ERR_UNSUPPORTED, "batched solves take rigid velocities");
+    // a context in the mobility mode (forces and torques prescribed) joins as a mobility problem,
+    // unless the batch brings its own rigid velocities
     if (ctxs[p]->device != c0->device) return c0->fail(MFS_ERR_ARG, "batched contexts must share one device");
     if (!io.repeats)
       for (int q = 0; q < p; ++q)
@@ -1198,13 +1215,15 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
     return c0->fail(MFS_ERR_ARG, "invalid solve options (restart must be in [1, 511])");
   check_state(c0, 2);
   // reuse the cached plan when the same contexts with the same builds come back
+  std::vector<int> mob(K, 0);
+  for (int p = 0; p < K; ++p) mob[p] = !io.v && ctxs[p]->mode == 1 ? 1 : 0;
   BatchPlan* B = c0->batch;
-  bool same = B && B->K == K;
+  bool same = B && B->K == K && B->mob == mob;
   for (int p = 0; same && p < K; ++p) same = B->key[p] == ctxs[p] && B->key_build[p] == ctxs[p]->build_id;
   if (!same) {
     if (B) delete B;
     c0->batch = nullptr;
-    mfs_status s = make_plan(c0, K, ctxs, B);
+    mfs_status s = make_plan(c0, K, ctxs, mob, B);
     if (s != MFS_OK) return s;
     c0->batch = B;
   }
@@ -1223,6 +1242,12 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
       if (!io.v[p] || !io.w[p]) return c0->fail(MFS_ERR_ARG, "null boundary data in the batch");
       CUDA_TRY(c0, cudaMemcpyAsync(B->bc_v + B->boff[p], io.v[p], bytes, kind, R.st));
       CUDA_TRY(c0, cudaMemcpyAsync(B->bc_w + B->boff[p], io.w[p], bytes, kind, R.st));
+    } else if (mob[p]) {
+      // fixed spheres in the background flow, then the prescribed (scaled) forces and torques
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_v + B->boff[p], c->d_zero, bytes, cudaMemcpyDeviceToDevice, R.st));
+      CUDA_TRY(c0, cudaMemcpyAsync(B->bc_w + B->boff[p], c->d_zero, bytes, cudaMemcpyDeviceToDevice, R.st));
+      CUDA_TRY(c0, cudaMemcpyAsync(B->wb + B->voff[p] + B->nlen[p], c->d_border, sizeof(double) * 6 * c->P,
+                                   cudaMemcpyDeviceToDevice, R.st));
     } else {
       CUDA_TRY(c0, cudaMemcpyAsync(B->bc_v + B->boff[p], c->d_v, bytes, cudaMemcpyDeviceToDevice, R.st));
       CUDA_TRY(c0, cudaMemcpyAsync(B->bc_w + B->boff[p], c->d_om, bytes, cudaMemcpyDeviceToDevice, R.st));
@@ -1310,7 +1335,16 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
   for (int p = 0; p < K; ++p) {
     mfs_ctx* c = ctxs[p];
     // each context keeps the solution of its last problem in the batch
-    CUDA_TRY(c0, cudaMemcpyAsync(c->d_mu, B->x + B->voff[p], sizeof(double) * c->n, cudaMemcpyDeviceToDevice, R.st));
+    CUDA_TRY(c0, cudaMemcpyAsync(c->d_mu, B->x + B->voff[p], sizeof(double) * (B->voff[p + 1] - B->voff[p]),
+                                 cudaMemcpyDeviceToDevice, R.st));
+    if (B->mob[p]) {
+      // rigid velocities from the border unknowns (V_k, Omega_k) per sphere
+      const double* xb = B->x + B->voff[p] + B->nlen[p];
+      CUDA_TRY(c0, cudaMemcpy2DAsync(c->d_v, 3 * sizeof(double), xb, 6 * sizeof(double), 3 * sizeof(double), c->P,
+                                     cudaMemcpyDeviceToDevice, R.st));
+      CUDA_TRY(c0, cudaMemcpy2DAsync(c->d_om, 3 * sizeof(double), xb + 3, 6 * sizeof(double), 3 * sizeof(double), c->P,
+                                     cudaMemcpyDeviceToDevice, R.st));
+    }
     CUDA_TRY(c0, cudaMemcpyAsync(c->d_lam, B->lam + B->uoff[p], sizeof(double) * c->n_unk, cudaMemcpyDeviceToDevice, R.st));
     launch_forces_torques(c->src, B->lam + B->uoff[p], B->out_F + B->boff[p], B->out_T + B->boff[p], R.st);
     const size_t bytes = sizeof(double) * 3 * c->P;
@@ -2788,10 +2822,12 @@ mfs_status mfs_tune_pairs(mfs_ctx* c, mfs_pair_shapes* out) {
     ms = t / 2.0;
     return MFS_OK;
   };
-  const PairShape cands[4] = {{1, 1}, {1, 0}, {4, 1}, {4, 0}};  // parts 0: the wave-filling rule
-  auto tune = [&](auto&& launch_with, PairShape& best, double& best_ms) -> mfs_status {
+  // parts 0: the wave-filling rule; packed -1: the scalar far kernel
+  const std::vector<PairShape> cands = {{1, 1, 0}, {1, 0, 0}, {4, 1, 0}, {4, 0, 0}};
+  const std::vector<PairShape> far_cands = {{1, 1, 0}, {1, 0, 0}, {4, 1, 0}, {4, 0, 0}, {4, 1, -1}, {4, 0, -1}};
+  auto tune = [&](auto&& launch_with, PairShape& best, double& best_ms, const std::vector<PairShape>& cs) -> mfs_status {
     best_ms = -1;
-    for (const PairShape& sh : cands) {
+    for (const PairShape& sh : cs) {
       if (sh.nt == 1 && c->tg.n_tiles1 == 0) continue;
       double ms = 0;
       mfs_status st = time_it([&] { launch_with(sh); }, ms);
@@ -2808,7 +2844,7 @@ mfs_status mfs_tune_pairs(mfs_ctx* c, mfs_pair_shapes* out) {
   PairShape best;
   if ((s = tune([&](PairShape sh) { launch_pairs_dw(c->tg, c->src, c->d_lh64, c->d_mu, c->d_w64, visc, c->d_pparts,
                                                     kPairMaxParts, c->stream, sh); },
-                best, ms)) != MFS_OK)
+                best, ms, cands)) != MFS_OK)
     return s;
   c->shape_all = best;
   PairShape ra = resolve_dw_shape(c->tg, c->src, best, kPairMaxParts);
@@ -2818,7 +2854,7 @@ mfs_status mfs_tune_pairs(mfs_ctx* c, mfs_pair_shapes* out) {
   if (c->ff.n_eq > 0) {
     if ((s = tune([&](PairShape sh) { launch_pairs_dw_near(c->tg, c->src, c->ff, c->d_lh64, c->d_mu, c->d_w64, visc,
                                                            c->d_pparts, kPairMaxParts, c->stream, sh); },
-                  best, ms)) != MFS_OK)
+                  best, ms, cands)) != MFS_OK)
       return s;
     c->shape_near = best;
     PairShape rn = resolve_near_shape(c->tg, best, kPairMaxParts);
@@ -2827,12 +2863,13 @@ mfs_status mfs_tune_pairs(mfs_ctx* c, mfs_pair_shapes* out) {
     r.near_ms = ms;
     if ((s = tune([&](PairShape sh) { launch_pairs_far(c->tg, c->src, c->ff, c->d_w64, visc, c->d_pparts,
                                                        kPairMaxParts, c->stream, sh); },
-                  best, ms)) != MFS_OK)
+                  best, ms, far_cands)) != MFS_OK)
       return s;
     c->shape_far = best;
     PairShape rf = resolve_far_shape(c->tg, best, kPairMaxParts);
     r.far_nodes_per_thread = rf.nt;
     r.far_parts = rf.parts;
+    r.far_packed = rf.packed;
     r.far_ms = ms;
   }
   c->solved = false;  // the work buffers were overwritten

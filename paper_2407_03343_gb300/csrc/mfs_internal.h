@@ -136,6 +136,7 @@ void launch_tc_gemm(const TcGemm& g, int ncols, const double* x, const long long
 struct PairShape {
   int nt = 0;
   int parts = 0;
+  int packed = 0;  // far kernel with 4 nodes per thread: 0 packed-FP32 (default), -1 scalar; resolved: 1 / 0
 };
 
 // Kernel launchers (mfs_kernels.cu).  All run on `st`.
@@ -186,7 +187,7 @@ struct SegTable;
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
-                          long long pstride, const SegTable& seg, cudaStream_t st);
+                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen = nullptr);
 
 // Batched GEMV: for every job j, y_j = M_j x_j with M_j row-major (rows_j x cols_j, leading dim ld_j).
 template <typename T>

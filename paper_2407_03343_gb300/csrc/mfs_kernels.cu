@@ -824,6 +824,149 @@ __global__ void __launch_bounds__(kPairThreads) pairs_far_kernel(FarArgs A, int 
   }
 }
 
+// Packed-FP32 variant (sm_100+ f32x2 instructions): the four targets of a thread form two pairs,
+// each operation of the pair math runs on both lanes of a pair with one instruction (the FMA pipe
+// still does one lane-operation per target, but the issue slots are halved, which is what bounds
+// the scalar kernel).  Sources are staged with every component duplicated into both lanes.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2sub(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2fma(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x f2make(float lo, float hi) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2split(f2x v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__global__ void __launch_bounds__(kPairThreads) pairs_far2_kernel(FarArgs A, int nparts, double* __restrict__ partial,
+                                                                  long long pstride) {
+  __shared__ ulonglong2 sa[kTileFar];  // (px, px | py, py)
+  __shared__ ulonglong2 sb[kTileFar];  // (pz, pz | fx, fx)
+  __shared__ ulonglong2 sc[kTileFar];  // (fy, fy | fz, fz)
+  constexpr int NT = 4;
+  const int t = blockIdx.x / nparts, part = blockIdx.x % nparts;
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift32 sh;
+  sh.hi = A.cen_hi;
+  sh.lo = A.cen_lo;
+  sh.init(k);
+  float x[NT], y[NT], z[NT], sx[NT], sy[NT], sz[NT], cx[NT], cy[NT], cz[NT];
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    float4 p = A.tgt[start + (idx < cnt ? idx : cnt - 1)];
+    x[q] = p.x; y[q] = p.y; z[q] = p.z;
+    sx[q] = sy[q] = sz[q] = cx[q] = cy[q] = cz[q] = 0.f;
+  }
+  const f2x X0 = f2make(x[0], x[1]), X1 = f2make(x[2], x[3]);
+  const f2x Y0 = f2make(y[0], y[1]), Y1 = f2make(y[2], y[3]);
+  const f2x Z0 = f2make(z[0], z[1]), Z1 = f2make(z[2], z[3]);
+  const f2x zero2 = f2make(0.f, 0.f);
+  const int e0 = A.excl_off[k], e1 = A.excl_off[k + 1];
+  const long long n_far = (long long)(A.P - (e1 - e0)) * A.n_eq;
+  const long long f0 = n_far * part / nparts, f1 = n_far * (part + 1) / nparts;
+  long long before = 0;
+  int prev = -1;
+  for (int a = e0; a <= e1; ++a) {
+    const int nxt = a < e1 ? A.excl_idx[a] : A.P;
+    const int run_lo = (prev + 1) * A.n_eq, run_hi = nxt * A.n_eq;
+    prev = nxt;
+    const long long len = run_hi - run_lo;
+    const int lo = run_lo + (int)max(0LL, min(len, f0 - before));
+    const int hi = run_lo + (int)max(0LL, min(len, f1 - before));
+    before += len;
+    for (int s0 = lo; s0 < hi; s0 += kTileFar) {
+      const int ns = min(kTileFar, hi - s0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < ns; i += kPairThreads) {
+        const int j = s0 + i;
+        const int o = j / A.n_eq;
+        const int e = j - o * A.n_eq;
+        const float4 z0 = A.eq[e];
+        const float px = z0.x + sh.d(o, 0), py = z0.y + sh.d(o, 1), pz = z0.z + sh.d(o, 2);
+        const float* g = A.q + 3LL * j;
+        const float fx = g[0], fy = g[1], fz = g[2];
+        sa[i] = make_ulonglong2(f2make(px, px), f2make(py, py));
+        sb[i] = make_ulonglong2(f2make(pz, pz), f2make(fx, fx));
+        sc[i] = make_ulonglong2(f2make(fy, fy), f2make(fz, fz));
+      }
+      __syncthreads();
+      f2x ux0 = zero2, uy0 = zero2, uz0 = zero2, ux1 = zero2, uy1 = zero2, uz1 = zero2;
+#pragma unroll 2
+      for (int j = 0; j < ns; ++j) {
+        const ulonglong2 a2 = sa[j], b2 = sb[j], c2 = sc[j];
+#define MFS_FAR2_PAIR(X, Y, Z, UX, UY, UZ)                                        \
+  {                                                                               \
+    const f2x dx = f2sub(X, a2.x), dy = f2sub(Y, a2.y), dz = f2sub(Z, b2.x);      \
+    const f2x r2 = f2fma(dz, dz, f2fma(dy, dy, f2mul(dx, dx)));                   \
+    float rl, rh;                                                                 \
+    f2split(r2, rl, rh);                                                          \
+    const f2x ir = f2make(rsqrtf(rl), rsqrtf(rh));                                \
+    const f2x ir2 = f2mul(ir, ir);                                                \
+    const f2x rf = f2fma(dz, c2.y, f2fma(dy, c2.x, f2mul(dx, b2.y)));             \
+    const f2x cc = f2mul(rf, ir2);                                                \
+    UX = f2fma(ir, f2fma(cc, dx, b2.y), UX);                                      \
+    UY = f2fma(ir, f2fma(cc, dy, c2.x), UY);                                      \
+    UZ = f2fma(ir, f2fma(cc, dz, c2.y), UZ);                                      \
+  }
+        MFS_FAR2_PAIR(X0, Y0, Z0, ux0, uy0, uz0)
+        MFS_FAR2_PAIR(X1, Y1, Z1, ux1, uy1, uz1)
+#undef MFS_FAR2_PAIR
+      }
+      float u[3][NT];
+      f2split(ux0, u[0][0], u[0][1]);
+      f2split(ux1, u[0][2], u[0][3]);
+      f2split(uy0, u[1][0], u[1][1]);
+      f2split(uy1, u[1][2], u[1][3]);
+      f2split(uz0, u[2][0], u[2][1]);
+      f2split(uz1, u[2][2], u[2][3]);
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        comp_add(sx[q], cx[q], u[0][q]);
+        comp_add(sy[q], cy[q], u[1][q]);
+        comp_add(sz[q], cz[q], u[2][q]);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    int idx = threadIdx.x + q * kPairThreads;
+    if (idx < cnt) {
+      long long node = start + idx;
+      double sw = A.tgt64[4 * node + 3] * (double)A.scale;
+      const double gx = sw * ((double)sx[q] + (double)cx[q]), gy = sw * ((double)sy[q] + (double)cy[q]),
+                   gz = sw * ((double)sz[q] + (double)cz[q]);
+      if (nparts > 1) {
+        double* o = partial + part * pstride + 3 * node;
+        o[0] = gx;
+        o[1] = gy;
+        o[2] = gz;
+      } else {
+        A.out[3 * node] += gx;
+        A.out[3 * node + 1] += gy;
+        A.out[3 * node + 2] += gz;
+      }
+    }
+  }
+}
+
 // out[e] (+)= the parts in order: with mu, out = mu + sqrt(w) * sum (the near kernel's unscaled
 // parts); without, out += sum (the far kernel's parts, already scaled)
 __global__ void parts_add_kernel(long long n3, const D4* __restrict__ tgt, int nparts, const double* __restrict__ partial,
@@ -871,6 +1014,7 @@ struct BatchVecs {
   const long long* voff;
   double* partial;     // split sources: nparts slices of the concatenated vector length
   long long pstride;
+  const long long* nlen;  // node rows (3 n_colloc) of each problem; a mobility problem's border follows
 };
 template <typename T, int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArgs<T>* __restrict__ args,
@@ -906,6 +1050,7 @@ __global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double
   if (!t.active[p]) return;
   const long long e = t.start[b] + (long long)blockIdx.y * blockDim.x + threadIdx.x;
   if (e >= t.end[b]) return;
+  if (bv.nlen && e - bv.voff[p] >= bv.nlen[p]) return;  // a mobility problem's border rows
   const D4* tgt = args[p].tgt;
   double s = 0.0;
   for (int q = 0; q < nparts; ++q) s += bv.partial[q * bv.pstride + e];
@@ -1637,10 +1782,12 @@ void launch_pairs_dw_near(const TargetSet& tg, const SourceSet& src, const FarFi
 PairShape resolve_far_shape(const TargetSet& tg, PairShape shape, int max_parts) {
   PairShape r;
   r.nt = shape_nt(tg, shape);
+  // 4 nodes per thread run the packed-FP32 kernel unless the scalar one is asked for
+  r.packed = r.nt == 4 && shape.packed >= 0 ? 1 : 0;
   const long long tiles = r.nt == 4 ? tg.n_tiles : tg.n_tiles1;
-  r.parts = shape.parts > 0 ? std::min(shape.parts, max_parts)
-                            : wave_parts(tiles, r.nt == 4 ? (const void*)pairs_far_kernel<4> : (const void*)pairs_far_kernel<1>,
-                                         max_parts);
+  const void* kern = r.nt == 4 ? (r.packed ? (const void*)pairs_far2_kernel : (const void*)pairs_far_kernel<4>)
+                               : (const void*)pairs_far_kernel<1>;
+  r.parts = shape.parts > 0 ? std::min(shape.parts, max_parts) : wave_parts(tiles, kern, max_parts);
   return r;
 }
 
@@ -1669,7 +1816,8 @@ void launch_pairs_far(const TargetSet& tg, const SourceSet& src, const FarField&
   const int parts = partial ? r.parts : 1;
   const long long n3 = 3LL * tg.n;
   ++t_launches;
-  if (nt == 4) pairs_far_kernel<4><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  if (nt == 4 && r.packed) pairs_far2_kernel<<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
+  else if (nt == 4) pairs_far_kernel<4><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
   else pairs_far_kernel<1><<<tiles * parts, kPairThreads, 0, st>>>(A, parts, partial, n3);
   if (parts > 1) {
     ++t_launches;
@@ -1689,10 +1837,10 @@ void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src,
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
-                          long long pstride, const SegTable& seg, cudaStream_t st) {
+                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen) {
   if (n_work == 0) return;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args);
-  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride};
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
   ++t_launches;
   if (double_float) {
     if (nodes_per_thread == 4) {

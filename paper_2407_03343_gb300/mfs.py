@@ -73,7 +73,7 @@ class Timing(C.Structure):
 class PairShapes(C.Structure):
     _fields_ = [("all_nodes_per_thread", C.c_int), ("all_parts", C.c_int), ("near_nodes_per_thread", C.c_int),
                 ("near_parts", C.c_int), ("far_nodes_per_thread", C.c_int), ("far_parts", C.c_int),
-                ("all_ms", C.c_double), ("near_ms", C.c_double), ("far_ms", C.c_double)]
+                ("far_packed", C.c_int), ("all_ms", C.c_double), ("near_ms", C.c_double), ("far_ms", C.c_double)]
 
 
 class MfsError(RuntimeError):

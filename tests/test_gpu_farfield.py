@@ -132,3 +132,26 @@ def test_autotuned_shapes_keep_the_operator(dilute):
     # other tiles and source splits only reorder the sums
     assert np.abs(after - before).max() <= 1e-9 * np.abs(before).max()
     assert np.abs(after - op.apply(mu)).max() <= 1e-5 * np.abs(before).max()
+
+
+def test_far_field_with_512_node_tiles():
+    # 343 contact-free spheres on a lattice 3 radii apart: enough 512-node tiles that the far
+    # kernel runs 4 nodes per thread (packed two-lane FP32 by default); the pass operator against
+    # the exact double-float operator, which the other tests tie to the oracle
+    g = np.arange(7) * 3.0
+    centres = np.array([[x, y, z] for x in g for y in g for z in g])
+    with mfs.Context(0) as ctx:
+        ctx.set_spheres(centres)
+        ctx.build(n_proxy=160, r_proxy=0.63, m_basic=480, **FAR)
+        s = ctx.sizes()
+        assert s.pairs_far_eq > 10 * s.pairs_near_fp
+        v, om = workloads.rigid_velocities(len(centres), seed=2)
+        ctx.set_rigid_velocities(v, om)
+        mu = ctx.rhs()
+        exact = ctx.apply_operator(mu, mfs.MIXED)
+        packed = ctx.apply_operator(mu, mfs.MIXED_PASS)
+        assert np.abs(packed - exact).max() <= 1e-5 * np.abs(exact).max()
+        shapes = ctx.tune_pairs()
+        tuned = ctx.apply_operator(mu, mfs.MIXED_PASS)
+        assert np.abs(tuned - exact).max() <= 1e-5 * np.abs(exact).max()
+        assert shapes.far_packed in (0, 1)

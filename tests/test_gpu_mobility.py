@@ -125,7 +125,7 @@ def test_mobility_errors(pair):
     with pytest.raises(mfs.MfsError, match="UNSUPPORTED"):
         ctx.solve(precision="fp32")
     with pytest.raises(mfs.MfsError, match="UNSUPPORTED"):
-        mfs.batch_solve([ctx], precision="mixed")
+        mfs.batch_solve([ctx], precision="fp32")
     # zero data: the solve returns zero velocities without iterating
     ctx.set_forces_torques(np.zeros((2, 3)), np.zeros((2, 3)))
     info = ctx.solve(precision="mixed")
@@ -151,3 +151,49 @@ def test_free_sphere_follows_linear_flow():
     curl = np.array([E[2, 1] - E[1, 2], E[0, 2] - E[2, 0], E[1, 0] - E[0, 1]])
     assert np.allclose(V[0], U + E @ c + np.cross(w, c), atol=1e-6)
     assert np.allclose(W[0], w + 0.5 * curl, atol=1e-6)
+
+
+def test_batched_mobility_matches_single_solves():
+    # mobility problems (forces and torques prescribed, velocities found) and a resistance problem
+    # in one lockstep batch: each must reproduce its own single solve, which the tests above tie
+    # to the oracle's dense bordered system
+    rng = np.random.default_rng(21)
+    kw = dict(n_proxy=120, r_proxy=0.63, m_basic=240)
+    geoms = [workloads.two_spheres(0.05), workloads.suspension(4, 0.15, seed=11), np.array([[0.0, 0.0, 0.0]]),
+             workloads.two_spheres(0.2)]
+    ctxs, loads = [], []
+    for i, c in enumerate(geoms):
+        ctx = mfs.Context(0)
+        ctx.set_spheres(c)
+        ctx.build(**kw)
+        P = c.shape[0]
+        if i < 3:
+            F, T = rng.normal(size=(P, 3)), rng.normal(size=(P, 3))
+            ctx.set_forces_torques(F, T)
+            loads.append(("mobility", F, T))
+        else:
+            v, w = rng.normal(size=(P, 3)), rng.normal(size=(P, 3))
+            ctx.set_rigid_velocities(v, w)
+            loads.append(("resistance", v, w))
+        ctxs.append(ctx)
+    infos = mfs.batch_solve(ctxs, precision="mixed", tol=1e-8)
+    assert all(i.converged == 1 for i in infos)
+    batch_out = []
+    for ctx, (kind, a, b) in zip(ctxs, loads):
+        batch_out.append(ctx.rigid_velocities() if kind == "mobility" else ctx.forces_torques())
+    for ctx, (kind, a, b), got in zip(ctxs, loads, batch_out):
+        if kind == "mobility":
+            ctx.set_forces_torques(a, b)
+        else:
+            ctx.set_rigid_velocities(a, b)
+        info = ctx.solve(precision="mixed", tol=1e-8)
+        assert info.converged == 1
+        ref = ctx.rigid_velocities() if kind == "mobility" else ctx.forces_torques()
+        scale = max(np.abs(ref[0]).max(), np.abs(ref[1]).max())
+        assert max(np.abs(got[0] - ref[0]).max(), np.abs(got[1] - ref[1]).max()) <= 1e-6 * scale, kind
+        if kind == "mobility":
+            # the forces and torques of the batched solution are the prescribed ones
+            F, T = ctx.forces_torques()
+            assert np.abs(F - a).max() <= 1e-6 * np.abs(a).max() and np.abs(T - b).max() <= 1e-6 * np.abs(b).max()
+    for ctx in ctxs:
+        ctx.close()
