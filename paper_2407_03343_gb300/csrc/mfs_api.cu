@@ -618,6 +618,9 @@ struct BatchPlan {
   int n_cwork = 0, n_cwork1 = 0;
   double* pparts = nullptr;  // source-split partial sums, kPairMaxParts * n_total
   std::vector<int> cprob_host;  // problem of each vector chunk
+  std::vector<int> jprob_host;  // problem of each GEMV job
+  int* d_jlist = nullptr;       // compacted GEMV job list of the active problems
+  int* jpin = nullptr;          // pinned staging for it
   int* d_cchunk = nullptr;      // compacted chunk list of the active problems (seg.list)
   int* cpin = nullptr;          // pinned staging for it
   GivensState gs;               // device GMRES state (restart_cap columns per problem)
@@ -645,6 +648,7 @@ struct BatchPlan {
     if (apin) cudaFreeHost(apin);
     if (wpin) cudaFreeHost(wpin);
     if (cpin) cudaFreeHost(cpin);
+    if (jpin) cudaFreeHost(jpin);
     if (snap) cudaFreeHost(snap);
     for (void* q : gs_allocs) cudaFree(q);
     if (ev) cudaEventDestroy(ev);
@@ -785,6 +789,9 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
   const float** dmA32 = nullptr;
   int *drA, *dcA, *dlA, *drV, *dcV, *dlV, *djp;
   long long *dxA, *dyA, *dxV, *dyV;
+  B->jprob_host = jp;
+  ok = ok && (B->d_jlist = B->alloc<int>(jp.size())) &&
+       cudaMallocHost(&B->jpin, sizeof(int) * std::max<size_t>(1, jp.size())) == cudaSuccess;
   ok = ok && put(B, dmA, mA) && put(B, dmV, mV) && put(B, drA, rA) && put(B, dcA, cA) && put(B, dlA, lA) &&
        put(B, drV, rV) && put(B, dcV, cV) && put(B, dlV, lV) && put(B, djp, jp) && put(B, dxA, xA) &&
        put(B, dyA, yA) && put(B, dxV, xV) && put(B, dyV, yV) && put(B, dmA2, mA2) && put(B, dmV2, mV2) &&
@@ -892,7 +899,18 @@ mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
   for (int b = 0; b < (int)B->cprob_host.size(); ++b)
     if (a[B->cprob_host[b]]) B->cpin[nc++] = b;
   B->seg.nlist = nc;
+  // GEMV jobs of the active problems (the launches' grids cover only those)
+  int nj = 0;
+  for (int j = 0; j < (int)B->jprob_host.size(); ++j)
+    if (a[B->jprob_host[j]]) B->jpin[nj++] = j;
+  for (GemvBatch<double>* g : {&B->gA, &B->gV}) {
+    g->job_list = B->d_jlist;
+    g->n_list = nj;
+  }
+  B->gA32.job_list = B->d_jlist;
+  B->gA32.n_list = nj;
   CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_active, B->apin, sizeof(int) * B->K, cudaMemcpyHostToDevice, R.st));
+  if (nj) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_jlist, B->jpin, sizeof(int) * nj, cudaMemcpyHostToDevice, R.st));
   if (nc) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cchunk, B->cpin, sizeof(int) * nc, cudaMemcpyHostToDevice, R.st));
   if (n4) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork, w4, sizeof(int2) * n4, cudaMemcpyHostToDevice, R.st));
   if (n1) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cwork1, w1, sizeof(int2) * n1, cudaMemcpyHostToDevice, R.st));

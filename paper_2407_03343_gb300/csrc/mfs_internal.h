@@ -203,6 +203,8 @@ struct GemvBatch {
   const int* job_prob = nullptr;  // optional: problem of each job, with
   const int* active = nullptr;    //   per-problem flags (jobs of inactive problems are skipped)
   const float2** mat_dw = nullptr;  // optional: the same matrices as (hi, lo) float pairs
+  const int* job_list = nullptr;    // optional: the jobs to run (n_list of them); the grid then
+  int n_list = 0;                   //   covers only those
 };
 template <typename T>
 void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st);

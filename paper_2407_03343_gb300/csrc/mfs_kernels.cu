@@ -1079,7 +1079,9 @@ template <typename T>
 __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, const T* __restrict__ x, T* __restrict__ y) {
   using VT = typename Vec<T>::type;
   constexpr int W = Vec<T>::w;
-  const int job = blockIdx.x;  // jobs sharing a matrix are adjacent, so its rows are read once
+  // jobs sharing a matrix are adjacent, so its rows are read once; with a compacted list the grid
+  // covers the active problems' jobs only
+  const int job = B.job_list ? B.job_list[blockIdx.x] : blockIdx.x;
   if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1122,7 +1124,9 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_kernel(GemvBatch<T> B, cons
 template <bool OUT64>
 __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double> B, const float2* __restrict__ x,
                                                                 float2* __restrict__ y2, double* __restrict__ y64) {
-  const int job = blockIdx.x;  // jobs sharing a matrix are adjacent, so its rows are read once
+  // jobs sharing a matrix are adjacent, so its rows are read once; with a compacted list the grid
+  // covers the active problems' jobs only
+  const int job = B.job_list ? B.job_list[blockIdx.x] : blockIdx.x;
   if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1194,7 +1198,7 @@ __global__ void __launch_bounds__(kGemvThreads) gemv_dw_kernel(GemvBatch<double>
 // accurate to ~1e-7; the refinement residual is evaluated with the double-float factors.
 __global__ void __launch_bounds__(kGemvThreads) gemv_f32dw_kernel(GemvBatch<float> B, const float2* __restrict__ x,
                                                                   float2* __restrict__ y2) {
-  const int job = blockIdx.x;
+  const int job = B.job_list ? B.job_list[blockIdx.x] : blockIdx.x;
   if (B.active && !B.active[B.job_prob[job]]) return;
   const int nr = B.rows[job], nc = B.cols[job], ld = B.ld[job];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1900,7 +1904,9 @@ template <typename T>
 void launch_gemv(const GemvBatch<T>& b, const T* x, T* y, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
-  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
+  const int jobs = b.job_list ? b.n_list : b.n_jobs;
+  if (jobs == 0) return;
+  dim3 grid(jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
   ++t_launches;
   gemv_kernel<T><<<grid, kGemvThreads, 0, st>>>(b, x, y);
 }
@@ -1909,7 +1915,9 @@ template void launch_gemv<float>(const GemvBatch<float>&, const float*, float*, 
 void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, double* y64, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
-  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
+  const int jobs = b.job_list ? b.n_list : b.n_jobs;
+  if (jobs == 0) return;
+  dim3 grid(jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
   ++t_launches;
   if (y_dw) gemv_dw_kernel<false><<<grid, kGemvThreads, 0, st>>>(b, x, y_dw, nullptr);
   else gemv_dw_kernel<true><<<grid, kGemvThreads, 0, st>>>(b, x, nullptr, y64);
@@ -1918,7 +1926,9 @@ void launch_gemv_dw(const GemvBatch<double>& b, const float2* x, float2* y_dw, d
 void launch_gemv_f32_dw(const GemvBatch<float>& b, const float2* x, float2* y_dw, cudaStream_t st) {
   if (b.n_jobs == 0 || b.max_rows == 0) return;
   const int rows_per_cta = (kGemvThreads / 32) * kGemvRowsPerWarp;
-  dim3 grid(b.n_jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
+  const int jobs = b.job_list ? b.n_list : b.n_jobs;
+  if (jobs == 0) return;
+  dim3 grid(jobs, (b.max_rows + rows_per_cta - 1) / rows_per_cta);
   ++t_launches;
   gemv_f32dw_kernel<<<grid, kGemvThreads, 0, st>>>(b, x, y_dw);
 }
