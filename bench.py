@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=SWEEP_TOL, help="GMRES tolerance of the timed solves")
     ap.add_argument("--kernel-case", type=int, default=0,
                     help="profiling case: build the sweep, run this many batched GMRES iterations, exit")
-    ap.add_argument("--profile-case", default="", choices=["", "far", "tensor"],
+    ap.add_argument("--profile-case", default="", choices=["", "far", "tensor", "gemv_rhs"],
                     help="profiling case: 'far' = pass-operator applies on a 343-sphere lattice with the far field, "
                          "'tensor' = the same on 60 contact-free spheres with the tensor-core step 1; then exit")
     ap.add_argument("--suspension", type=int, default=200,
@@ -242,13 +242,13 @@ def suspension_kernel_rates(device, fp32_peak):
     return out
 
 
-FAR = dict(far_dist=4.0, far_n_eq=300, far_r_eq=1.0, far_r_chk=2.0, far_eps=1e-6)
+FAR = dict(far_dist=3.5, far_n_eq=300, far_r_eq=1.0, far_r_chk=2.0, far_eps=1e-6)
 
 
 def suspension_solve(device, P=200, tol=SWEEP_TOL):
     """The random suspension (P unit spheres at volume fraction 0.2, near contacts at gaps
     log-uniform in [1e-3, 1e-1], N = 800, M0 = 1600, random rigid motions) solved in MIXED
-    precision with the far field in the GMRES passes (spheres more than 4 radii apart through 300
+    precision with the far field in the GMRES passes (spheres more than 3.5 radii apart through 300
     equivalent Stokeslets) and the exact double-float operator in the refinement residual.  The
     solve is timed with CUDA events on the context's stream; the operator applies of the passes,
     of the exact double-float operator and of the plain FP64 operator are timed per launch."""
@@ -366,8 +366,25 @@ def cluster_example(device, P=100, delta=1e-2, r_proxy=0.75, far=False):
 
 
 def profile_case(kind, device):
-    """Small cases for ncu captures of the far-field and tensor-core kernels (two pass applies)."""
+    """Small cases for ncu captures: the far-field and tensor-core kernels (two pass applies), and
+    the step-1 GEMVs of three right-hand sides per geometry (three gap-sweep geometries with the
+    three motions each, four lockstep iterations; ~2 GB of factors)."""
     from paper_2407_03343_gb300 import mfs, workloads
+    if kind == "gemv_rhs":
+        ctxs = []
+        for gap in (1e-3, 1e-2, 1e-1):
+            c = mfs.Context(device)
+            c.set_spheres(workloads.two_spheres(gap))
+            c.build(n_proxy=N_PROXY, r_proxy=R_PROXY, m_basic=M_BASIC)
+            ctxs.append(c)
+        probs = [c for _ in MOTIONS for c in ctxs]
+        vel = [workloads.motion(m) for m in MOTIONS for _ in ctxs]
+        mfs.batch_solve_rhs(probs, vel, mfs.default_solve_opts(precision="mixed", tol=1e-12, max_iter=4, max_refine=1),
+                            allow_not_converged=True)
+        for c in ctxs:
+            c.close()
+        print(json.dumps({"profile_case": kind}))
+        return
     ctx = mfs.Context(device)
     if kind == "far":
         # 343 spheres on a 7 x 7 x 7 lattice 3 radii apart (no contacts: one shared factor, little

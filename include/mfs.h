@@ -165,6 +165,12 @@ typedef struct {
                          an image S+R+D triple counts as 3 */
   long long pairs_near_fp;  /* with the far field: of those, the pairs with near spheres (double-float) */
   long long pairs_far_eq;   /* and the (target node, equivalent Stokeslet) pairs replacing the rest (FP32) */
+  int n_factors_shared;     /* factors of spheres without images: these live in a process-wide store
+                               per device and are shared with every context whose spheres have the same
+                               self block (same radius, viscosity, proxy and collocation grids,
+                               truncation and far-field settings), so equal spheres need one SVD across
+                               contexts (Sec. 4); each holder counts them in its memory use */
+  int n_factors_reused;     /* of those, the factors this build took from the store instead of computing */
 } mfs_sizes_t;
 
 void mfs_default_params(mfs_params* p);
@@ -353,6 +359,10 @@ typedef struct {
   long long far_launches;
   double far_ms;
   long long far_pairs;
+  /* tensor-core step 1 (spheres sharing the basic factor): matrix products launched and the
+   * sphere columns they covered */
+  long long tc_launches;
+  long long tc_columns;
 } mfs_timing_t;
 mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
 /* Copies the counters; reset != 0 zeroes them afterwards. */

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -68,6 +69,15 @@ __global__ void pack_A_kernel(int r, int m, int ld, const double* __restrict__ U
   }
 }
 
+// R (n x n, leading dimension n) = the upper triangle of the QR-factored B (leading dimension ldb)
+__global__ void upper_copy_kernel(int n, const double* __restrict__ B, int ldb, double* __restrict__ R) {
+  const long long tot = (long long)n * n;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < tot; id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % n), j = (int)(id / n);
+    R[id] = i <= j ? B[(long long)j * ldb + i] : 0.0;
+  }
+}
+
 // VT is the column-major ncol x ncol matrix V^T returned by the SVD: V(row, i) = VT[row * ncol + i]
 __global__ void pack_V_kernel(int ncol, int r, int ld, const double* __restrict__ VT, const int* __restrict__ keep,
                               double* __restrict__ V64, float* __restrict__ V32, float2* __restrict__ V2) {
@@ -79,6 +89,64 @@ __global__ void pack_V_kernel(int ncol, int r, int ld, const double* __restrict_
     V32[id] = (float)v;
     V2[id] = split2(v);
   }
+}
+
+// A one-body factor of a sphere without images, held by every context on the device whose
+// spheres have the same self block: equal spheres share one truncated pseudo-inverse across
+// contexts as they do within one (Sec. 4: a single SVD serves equal spheres).  The key holds
+// every input of the factorisation; the entry is freed with the last context that holds it.
+struct SharedFactor {
+  int device = 0;
+  std::vector<double> key;
+  Factor F;
+  std::vector<void*> mem;
+  unsigned long long bytes = 0;  // the factor's device memory
+  int q_rows = 0;                // rows of the far-field Q (3 n_eq), 0 without a far field
+  // bf16 slices of Sigma^+ U^T and of Q for the tensor-core step 1, made on first use
+  std::mutex tc_mtx;
+  int tc_ldk = 0;
+  void* as[3] = {nullptr, nullptr, nullptr};
+  void* qs[3] = {nullptr, nullptr, nullptr};
+  unsigned long long tc_bytes = 0;
+  void* alloc(size_t n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    mem.push_back(q);
+    return q;
+  }
+  ~SharedFactor() {
+    int d0 = 0;
+    const bool had = cudaGetDevice(&d0) == cudaSuccess;
+    cudaSetDevice(device);
+    for (void* q : mem) cudaFree(q);
+    if (had) cudaSetDevice(d0);
+    cudaGetLastError();
+  }
+};
+
+std::mutex g_store_mtx;
+std::vector<std::weak_ptr<SharedFactor>> g_store;
+
+std::shared_ptr<SharedFactor> store_find(int device, const std::vector<double>& key) {
+  std::lock_guard<std::mutex> g(g_store_mtx);
+  std::shared_ptr<SharedFactor> hit;
+  size_t w = 0;
+  for (size_t i = 0; i < g_store.size(); ++i) {
+    std::shared_ptr<SharedFactor> e = g_store[i].lock();
+    if (!e) continue;  // expired: dropped from the list
+    g_store[w++] = g_store[i];
+    if (!hit && e->device == device && e->key == key) hit = e;
+  }
+  g_store.resize(w);
+  return hit;
+}
+
+void store_add(const std::shared_ptr<SharedFactor>& e) {
+  std::lock_guard<std::mutex> g(g_store_mtx);
+  g_store.push_back(e);
 }
 
 }  // namespace
@@ -129,6 +197,10 @@ struct mfs_ctx {
   int* d_owner = nullptr;
   double* d_sqrtw = nullptr;
   std::vector<Factor> factors;
+  // factors of spheres without images, held in the process-wide store with every context that
+  // has the same self block (counted in mem_used by each holder)
+  std::vector<std::shared_ptr<SharedFactor>> shared;
+  int factors_reused = 0;  // of those, taken from the store instead of computed by this build
   FarField ff;             // n_eq == 0: no far field
   float* d_q = nullptr;    // equivalent strengths, 3 n_eq per sphere
   GemvBatch<float> gQ;     // q = Q_f mu_k for every sphere
@@ -193,6 +265,8 @@ struct mfs_ctx {
     alloc_bytes.clear();
     mem_used = 0;
     factors.clear();
+    shared.clear();
+    factors_reused = 0;
     ff = FarField();
     d_q = nullptr;
     gQ = GemvBatch<float>();
@@ -324,6 +398,8 @@ void precond(mfs_ctx* c, const T* mu, T* lam_hat) {
           launch_gemv_f32_dw(c->gA32_rest, c->d_x2, c->d_t2, c->stream);
           launch_tc_gemm(c->tcA, c->tc_ncols, mu, c->d_tc_xoff, c->d_tc_yA, nullptr, c->d_t2, c->d_tc_partial,
                          c->d_tc_err, true, c->stream);
+          c->tm.tc_launches += 1;
+          c->tm.tc_columns += c->tc_ncols;
         } else if (c->dw_fast_a) {
           launch_gemv_f32_dw(c->gA32, c->d_x2, c->d_t2, c->stream);
         } else {
@@ -358,6 +434,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
           launch_gemv<float>(c->gQ_rest, c->d_mu32, c->d_q, c->stream);
           launch_tc_gemm(c->tcQ, c->tc_ncols, mu, c->d_tc_xoff, c->d_tc_yQ, c->d_q, nullptr, c->d_tc_partial,
                          c->d_tc_err, true, c->stream);
+          c->tm.tc_launches += 1;
+          c->tm.tc_columns += c->tc_ncols;
         } else {
           launch_gemv<float>(c->gQ, c->d_mu32, c->d_q, c->stream);
         }
@@ -570,6 +648,33 @@ mfs_status norm64(mfs_ctx* c, const double* v, double& out) {
 }
 
 // A bounded wait of the tensor-core kernel ran out (its flag is cleared for the next call).
+// The bf16 slices of a store entry's Sigma^+ U^T (and of its far-field Q when it has one), made
+// once for every context that holds the entry; the calling context's cap counts them.
+mfs_status ensure_tc_slices(mfs_ctx* c, SharedFactor& e) {
+  std::lock_guard<std::mutex> g(e.tc_mtx);
+  const Factor& F = e.F;
+  const int ldk = tc_ldk(F.m);
+  if (!e.as[0]) {
+    const size_t b = sizeof(uint16_t) * (size_t)F.rank * ldk;
+    for (int i = 0; i < 3; ++i)
+      if (!(e.as[i] = e.alloc(b))) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
+    e.tc_bytes += 3 * b;
+    launch_split3_matrix(F.rank, F.m, F.ldA, F.A64, ldk, e.as[0], e.as[1], e.as[2], c->stream);
+  }
+  if (F.Q32 && !e.qs[0]) {
+    const int rows = e.q_rows;
+    const size_t b = sizeof(uint16_t) * (size_t)rows * ldk;
+    for (int i = 0; i < 3; ++i)
+      if (!(e.qs[i] = e.alloc(b))) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
+    e.tc_bytes += 3 * b;
+    launch_split3_matrix_f32(rows, F.m, F.ldQ, F.Q32, ldk, e.qs[0], e.qs[1], e.qs[2], c->stream);
+  }
+  e.tc_ldk = ldk;
+  CHECK_LAUNCH(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // other contexts' streams read them next
+  return MFS_OK;
+}
+
 mfs_status check_tc_timeout(mfs_ctx* c) {
   if (!c->d_tc_err) return MFS_OK;
   int h = 0;
@@ -630,6 +735,22 @@ struct BatchPlan {
   long long *d_uoff = nullptr, *d_voff = nullptr;
   GemvBatch<double> gA, gV;
   GemvBatch<float> gA32;  // the same jobs over the FP32 copies of Sigma^+ U^T (inner MIXED solves)
+  // tensor-core step 1 of the inner MIXED solves: the spheres of every problem whose factor is
+  // one store entry form the columns of one product; gA32 then covers the other jobs only
+  std::shared_ptr<SharedFactor> tc_ent;  // keeps the entry (and its slices) alive with the plan
+  TcGemm tcA;
+  int tc_ncap = 0, tc_nact = 0;
+  std::vector<int> tc_prob;                // problem of each column
+  std::vector<long long> tc_x_host, tc_y_host;
+  long long *d_tc_x = nullptr, *d_tc_y = nullptr;  // offsets of the active problems' columns
+  long long* tc_pin = nullptr;             // pinned staging for them (2 tc_ncap)
+  float* tc_partial = nullptr;
+  int* tc_err = nullptr;
+  std::vector<char> jtc_host;              // per GEMV job: 1 when it is a tensor column
+  std::vector<int> leader;                 // per problem: the first problem on the same context
+  std::vector<double> bA32_p, bA2_p, bV_p; // per context (at its leader): factor bytes of one step 1
+  int* d_jlist_rest = nullptr;             // compacted list of the active problems' other jobs
+  int* jpin_rest = nullptr;
   SegTable seg;
   double *wb = nullptr, *x = nullptr, *r = nullptr, *e = nullptr, *w = nullptr, *lh = nullptr, *tmp = nullptr,
          *lam = nullptr, *partial = nullptr, *hbuf = nullptr, *coef = nullptr, *scl = nullptr;
@@ -649,6 +770,8 @@ struct BatchPlan {
     if (wpin) cudaFreeHost(wpin);
     if (cpin) cudaFreeHost(cpin);
     if (jpin) cudaFreeHost(jpin);
+    if (tc_pin) cudaFreeHost(tc_pin);
+    if (jpin_rest) cudaFreeHost(jpin_rest);
     if (snap) cudaFreeHost(snap);
     for (void* q : gs_allocs) cudaFree(q);
     if (ev) cudaEventDestroy(ev);
@@ -751,7 +874,40 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
       ptoff[p].push_back(t);
     }
   }
+  // the store entry shared by most spheres over all problems (contexts built with
+  // tensor_step1 = 0 keep their spheres on the GEMV)
+  std::shared_ptr<SharedFactor> best;
+  {
+    std::vector<std::pair<SharedFactor*, int>> cnt;
+    bool any2 = false;
+    for (int p = 0; p < K; ++p) {
+      mfs_ctx* c = ctxs[p];
+      if (c->hd.prm.tensor_step1 == 0) continue;
+      any2 = any2 || c->hd.prm.tensor_step1 == 2;
+      for (int kk = 0; kk < c->hd.P; ++kk) {
+        const double* a64 = c->factors[c->hd.factor_id[kk]].A64;
+        for (auto& e : c->shared)
+          if (e->F.A64 == a64) {
+            size_t i = 0;
+            while (i < cnt.size() && cnt[i].first != e.get()) ++i;
+            if (i == cnt.size()) cnt.push_back({e.get(), 0});
+            ++cnt[i].second;
+          }
+      }
+    }
+    int bi = -1;
+    for (size_t i = 0; i < cnt.size(); ++i)
+      if (bi < 0 || cnt[i].second > cnt[bi].second) bi = (int)i;
+    if (bi >= 0 && cnt[bi].second >= (any2 ? 1 : 8))
+      for (int p = 0; p < K && !best; ++p)
+        for (auto& e : ctxs[p]->shared)
+          if (e.get() == cnt[bi].first) best = e;
+  }
   std::vector<int> seen(K, 0);
+  B->leader.assign(K, 0);
+  B->bA32_p.assign(K, 0.0);
+  B->bA2_p.assign(K, 0.0);
+  B->bV_p.assign(K, 0.0);
   for (int p0 = 0; p0 < K && ok; ++p0) {
     if (seen[p0]) continue;
     mfs_ctx* c = ctxs[p0];
@@ -761,9 +917,14 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
       if (ctxs[p] == c) {
         group.push_back(p);
         seen[p] = 1;
+        B->leader[p] = p0;
       }
     for (int k = 0; k < d.P; ++k) {
       const Factor& F = c->factors[d.factor_id[k]];
+      const bool tc_k = best && c->hd.prm.tensor_step1 != 0 && F.A64 == best->F.A64;
+      if (!tc_k) B->bA32_p[p0] += 4.0 * F.rank * F.m;
+      B->bA2_p[p0] += 8.0 * F.rank * F.m;
+      B->bV_p[p0] += 8.0 * F.ncol * F.rank;
       for (int p : group) {
         mA.push_back(F.A64);
         mV.push_back(F.V64);
@@ -779,6 +940,13 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
         jp.push_back(p);
         maxA = std::max(maxA, F.rank);
         maxV = std::max(maxV, F.ncol);
+        const bool tc = best && ctxs[p]->hd.prm.tensor_step1 != 0 && F.A64 == best->F.A64;
+        B->jtc_host.push_back(tc ? 1 : 0);
+        if (tc) {
+          B->tc_prob.push_back(p);
+          B->tc_x_host.push_back(xA.back());
+          B->tc_y_host.push_back(yA.back());
+        }
       }
     }
   }
@@ -806,6 +974,36 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
     B->gA32.mat = dmA32; B->gA32.rows = drA; B->gA32.cols = dcA; B->gA32.ld = dlA; B->gA32.x_off = dxA;
     B->gA32.y_off = dyA; B->gA32.n_jobs = (int)mA32.size(); B->gA32.max_rows = maxA; B->gA32.job_prob = djp;
     B->gA32.active = B->d_active;
+  }
+  if (ok && best) {
+    const Factor& F = best->F;
+    const int ncap = (int)B->tc_prob.size();
+    mfs_status st2 = ensure_tc_slices(c0, *best);
+    if (st2 != MFS_OK) {
+      delete B;
+      return st2;
+    }
+    void* xs[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i)
+      if (!(xs[i] = B->alloc<uint16_t>((size_t)ncap * tc_ldk(F.m)))) {
+        delete B;
+        return c0->fail(MFS_ERR_OOM, "device allocation failed: batch tensor-core slices");
+      }
+    if (!tc_prepare(B->tcA, best->as, F.rank, xs, ncap, F.m)) {
+      delete B;
+      return c0->fail(MFS_ERR_CUDA, "tensor-core step 1: tensor maps or shared-memory limit unavailable");
+    }
+    // the partial-sum buffer for any number of active columns up to ncap
+    size_t part = 0;
+    for (int n = 1; n <= ncap; ++n) part = std::max(part, tc_partial_floats(B->tcA, n));
+    B->tc_ent = best;
+    B->tc_ncap = ncap;
+    ok = (B->d_tc_x = B->alloc<long long>(ncap)) && (B->d_tc_y = B->alloc<long long>(ncap)) &&
+         (B->tc_partial = B->alloc<float>(part)) && (B->tc_err = B->alloc<int>(1)) &&
+         (B->d_jlist_rest = B->alloc<int>(jp.size())) &&
+         cudaMemset(B->tc_err, 0, sizeof(int)) == cudaSuccess &&
+         cudaMallocHost(&B->tc_pin, sizeof(long long) * 2 * ncap) == cudaSuccess &&
+         cudaMallocHost(&B->jpin_rest, sizeof(int) * std::max<size_t>(1, jp.size())) == cudaSuccess;
   }
   // vector chunks, each inside one problem
   const long long chunk = 1024;  // enough chunks to fill the GPU for batches of small problems
@@ -909,6 +1107,28 @@ mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
   }
   B->gA32.job_list = B->d_jlist;
   B->gA32.n_list = nj;
+  if (B->tc_ncap > 0) {
+    // the FP32 GEMV covers the jobs that are not tensor columns; the columns of the active
+    // problems go to the tensor-core product
+    int nr = 0, nt = 0;
+    for (int j = 0; j < (int)B->jprob_host.size(); ++j)
+      if (a[B->jprob_host[j]] && !B->jtc_host[j]) B->jpin_rest[nr++] = j;
+    for (int i = 0; i < B->tc_ncap; ++i)
+      if (a[B->tc_prob[i]]) {
+        B->tc_pin[nt] = B->tc_x_host[i];
+        B->tc_pin[B->tc_ncap + nt] = B->tc_y_host[i];
+        ++nt;
+      }
+    B->gA32.job_list = B->d_jlist_rest;
+    B->gA32.n_list = nr;
+    B->tc_nact = nt;
+    if (nr) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_jlist_rest, B->jpin_rest, sizeof(int) * nr, cudaMemcpyHostToDevice, R.st));
+    if (nt) {
+      CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_tc_x, B->tc_pin, sizeof(long long) * nt, cudaMemcpyHostToDevice, R.st));
+      CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_tc_y, B->tc_pin + B->tc_ncap, sizeof(long long) * nt, cudaMemcpyHostToDevice,
+                                     R.st));
+    }
+  }
   CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_active, B->apin, sizeof(int) * B->K, cudaMemcpyHostToDevice, R.st));
   if (nj) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_jlist, B->jpin, sizeof(int) * nj, cudaMemcpyHostToDevice, R.st));
   if (nc) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_cchunk, B->cpin, sizeof(int) * nc, cudaMemcpyHostToDevice, R.st));
@@ -926,8 +1146,17 @@ void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
   timed(c, c->ev_gemv, [&] {
     if (R.dw) {
       launch_split_dw(B->n_total, in, B->x2, R.st);
-      if (R.fast_a) launch_gemv_f32_dw(B->gA32, B->x2, B->t2, R.st);
-      else launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
+      if (R.fast_a) {
+        launch_gemv_f32_dw(B->gA32, B->x2, B->t2, R.st);
+        if (B->tc_nact > 0) {
+          launch_tc_gemm(B->tcA, B->tc_nact, in, B->d_tc_x, B->d_tc_y, nullptr, B->t2, B->tc_partial, B->tc_err, true,
+                         R.st);
+          c->tm.tc_launches += 1;
+          c->tm.tc_columns += B->tc_nact;
+        }
+      } else {
+        launch_gemv_dw(B->gA, B->x2, B->t2, nullptr, R.st);
+      }
       launch_gemv_dw(B->gV, B->t2, nullptr, B->lh, R.st);
     } else {
       launch_gemv<double>(B->gA, in, B->tmp, R.st);
@@ -975,6 +1204,7 @@ void batch_apply_count(BatchRun& R, const std::vector<int>& act) {
   mfs_ctx* c = R.c0;
   BatchPlan* B = R.B;
   const int kind = R.dw ? MFS_MIXED : MFS_FP64;
+  std::vector<int> per_ctx(B->K, 0);
   for (int p = 0; p < B->K; ++p)
     if (act[p]) {
       c->tm.pair_interactions += B->pairs_p[p];
@@ -982,8 +1212,12 @@ void batch_apply_count(BatchRun& R, const std::vector<int>& act) {
       c->tm.pair_image_nodes += B->image_p[p];
       c->tm.by_kind_proxy[kind] += B->proxy_p[p];
       c->tm.by_kind_image_nodes[kind] += B->image_p[p];
-      c->tm.gemv_bytes += R.dw && R.fast_a ? B->key[p]->gemv_bytes_fast : B->key[p]->gemv_bytes64;
+      ++per_ctx[B->leader[p]];
     }
+  // factor bytes: the right-hand sides on one geometry run their jobs of a factor in adjacent
+  // CTAs, which read it from HBM once (the others hit L2): one read per context and apply
+  for (int p = 0; p < B->K; ++p)
+    if (per_ctx[p] > 0) c->tm.gemv_bytes += (R.dw && R.fast_a ? B->bA32_p[p] : B->bA2_p[p]) + B->bV_p[p];
 }
 
 // Gram-Schmidt traffic of Arnoldi step j over the problems of `act`: two dot-product launches
@@ -1333,6 +1567,15 @@ mfs_status batch_lockstep_impl(int K, mfs_ctx* const* ctxs, const mfs_solve_opts
         if (outer > 0) ++refines[p];
         if (rel[p] >= prev && rel[p] > o.tol) stalled[p] = 1;  // a pass that gained nothing
       }
+    }
+  }
+  if (B->tc_err) {
+    int h = 0;
+    CUDA_TRY(c0, cudaMemcpyAsync(&h, B->tc_err, sizeof(int), cudaMemcpyDeviceToHost, R.st));
+    CUDA_TRY(c0, cudaStreamSynchronize(R.st));
+    if (h) {
+      CUDA_TRY(c0, cudaMemsetAsync(B->tc_err, 0, sizeof(int), R.st));
+      return c0->fail(MFS_ERR_TIMEOUT, "tensor-core step 1: a pipeline wait ran out of time");
     }
   }
   // lambda = B^+ mu, then per-context outputs
@@ -1789,18 +2032,27 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
       cleanup();
       return fail_w(MFS_ERR_CUDA, "factor worker: stream or cuSOLVER handle creation failed");
     }
-    int lwork = 0;
-    if (cusolverDnDgesvd_bufferSize(h, max_m, max_nc, &lwork) != CUSOLVER_STATUS_SUCCESS) {
-      cleanup();
-      return fail_w(MFS_ERR_CUDA, "cusolverDnDgesvd_bufferSize failed");
-    }
+    // B = QR (blocked Householder), R = U_R Sigma V^T (square SVD), U = Q [U_R; 0]: the route of
+    // LAPACK's SVD for tall matrices, backward stable like the SVD of B itself
     double* dB = (double*)salloc(sizeof(double) * (size_t)max_m * max_nc);
+    double* dR = (double*)salloc(sizeof(double) * (size_t)max_nc * max_nc);
+    double* dUR = (double*)salloc(sizeof(double) * (size_t)max_nc * max_nc);
+    double* dtau = (double*)salloc(sizeof(double) * max_nc);
+    int lwork = 0, lw_qr = 0, lw_orm = 0;
+    if (!dB || !dR || !dUR || !dtau || cusolverDnDgesvd_bufferSize(h, max_nc, max_nc, &lwork) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDgeqrf_bufferSize(h, max_m, max_nc, dB, max_m, &lw_qr) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnDormqr_bufferSize(h, CUBLAS_SIDE_LEFT, CUBLAS_OP_N, max_m, max_nc, max_nc, dB, max_m, dtau, dB, max_m,
+                                    &lw_orm) != CUSOLVER_STATUS_SUCCESS) {
+      cleanup();
+      return fail_w(MFS_ERR_CUDA, "factor worker: cuSOLVER workspace query failed");
+    }
+    lwork = std::max(lwork, std::max(lw_qr, lw_orm));
     double* dU = (double*)salloc(sizeof(double) * (size_t)max_m * max_nc);
     double* dVT = (double*)salloc(sizeof(double) * (size_t)max_nc * max_nc);
     double* dS = (double*)salloc(sizeof(double) * max_nc);
     double* drw = (double*)salloc(sizeof(double) * max_nc);
     double* dwork = (double*)salloc(sizeof(double) * (size_t)lwork);
-    int* dinfo = (int*)salloc(sizeof(int));
+    int* dinfo = (int*)salloc(3 * sizeof(int));
     double* dxr = (double*)salloc(sizeof(double) * (size_t)max_m);
     double* dsw = (double*)salloc(sizeof(double) * ((size_t)max_m / 3 + 1));
     double* dyr = (double*)salloc(sizeof(double) * (size_t)max_nc);
@@ -1853,6 +2105,48 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
           ty[base + t] = t;
         }
       }
+      // a sphere without images has the basic block, fixed by the radius, the viscosity, the
+      // proxy sphere (N, R_p), the basic grid (M0, its weights), the truncation and the far-field
+      // settings (the grids are global-frame, so the block does not depend on the centre): its
+      // factor may already be in the store; otherwise it is computed into a new store entry
+      std::shared_ptr<SharedFactor> ent;
+      if (d.img_off[k + 1] == d.img_off[k]) {
+        std::vector<double> key = {c->a,        p.visc,       p.eps_trunc,        (double)N,
+                                   p.r_proxy,   (double)p.m_basic, (double)p.left_precond, (double)m_nodes,
+                                   far_on ? 1.0 : 0.0, (double)n_eq, p.far_r_eq, p.far_r_chk,
+                                   p.far_eps};
+        if (std::shared_ptr<SharedFactor> hit = store_find(c->device, key)) {
+          std::lock_guard<std::mutex> g(mtx);
+          if (c->mem_limit && c->mem_used + hit->bytes > c->mem_limit) {
+            if (wstat == MFS_OK) {
+              wstat = MFS_ERR_OOM;
+              werr = "device allocation failed: one-body factors (memory cap)";
+            }
+            break;
+          }
+          c->mem_used += hit->bytes;
+          c->shared.push_back(hit);
+          c->factors[f] = hit->F;
+          ++c->factors_reused;
+          continue;
+        }
+        ent = std::make_shared<SharedFactor>();
+        ent->device = c->device;
+        ent->key = std::move(key);
+        ent->q_rows = far_on ? 3 * n_eq : 0;
+      }
+      // device memory of the factor: the context's own, or the new store entry's (held by the
+      // context and counted against its cap)
+      auto falloc = [&](size_t bytes) -> void* {
+        if (!ent) return c->dalloc<char>(bytes);
+        if (c->mem_limit && c->mem_used + bytes > c->mem_limit) return nullptr;
+        void* q = ent->alloc(bytes);
+        if (q) {
+          c->mem_used += bytes;
+          ent->bytes += bytes;
+        }
+        return q;
+      };
       cudaError_t e1 = cudaMemcpyAsync(dxr, xr.data(), xr.size() * 8, cudaMemcpyHostToDevice, st);
       cudaError_t e2 = cudaMemcpyAsync(dsw, swk.data(), swk.size() * 8, cudaMemcpyHostToDevice, st);
       cudaError_t e3 = cudaMemcpyAsync(dyr, yr.data(), yr.size() * 8, cudaMemcpyHostToDevice, st);
@@ -1862,17 +2156,22 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
         break;
       }
       launch_assemble_self(d, k, dxr, dsw, dyr, dty, n_src, dB, m, st);
-      int lw = 0;
-      cusolverDnDgesvd_bufferSize(h, m, ncol, &lw);
-      if (lw > lwork) {
-        fail_w(MFS_ERR_CUDA, "SVD workspace larger than the one sized for the largest block");
-        break;
-      }
-      cusolverStatus_t sst = cusolverDnDgesvd(h, 'S', 'S', m, ncol, dB, m, dS, dU, m, dVT, ncol, dwork, lwork, drw, dinfo);
-      int hinfo = 0;
-      cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cusolverStatus_t sst = cusolverDnDgeqrf(h, m, ncol, dB, m, dtau, dwork, lwork, dinfo);
+      upper_copy_kernel<<<256, 256, 0, st>>>(ncol, dB, m, dR);
+      if (sst == CUSOLVER_STATUS_SUCCESS)
+        sst = cusolverDnDgesvd(h, 'S', 'S', ncol, ncol, dR, ncol, dS, dUR, ncol, dVT, ncol, dwork, lwork, drw, dinfo + 1);
+      // U = Q [U_R; 0]
+      cudaMemsetAsync(dU, 0, sizeof(double) * (size_t)m * ncol, st);
+      cudaMemcpy2DAsync(dU, sizeof(double) * m, dUR, sizeof(double) * ncol, sizeof(double) * ncol, ncol,
+                        cudaMemcpyDeviceToDevice, st);
+      if (sst == CUSOLVER_STATUS_SUCCESS)
+        sst = cusolverDnDormqr(h, CUBLAS_SIDE_LEFT, CUBLAS_OP_N, m, ncol, ncol, dB, m, dtau, dU, m, dwork, lwork,
+                               dinfo + 2);
+      int hinfo3[3] = {0, 0, 0};
+      cudaMemcpyAsync(hinfo3, dinfo, 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaMemcpyAsync(hS.data(), dS, sizeof(double) * ncol, cudaMemcpyDeviceToHost, st);
       cudaError_t es = cudaStreamSynchronize(st);
+      const int hinfo = hinfo3[0] ? hinfo3[0] : (hinfo3[1] ? hinfo3[1] : hinfo3[2]);
       if (sst != CUSOLVER_STATUS_SUCCESS || es != cudaSuccess || hinfo != 0) {
         fail_w(MFS_ERR_CUDA, "one-body SVD failed (cusolver status " + std::to_string((int)sst) + ", info " +
                                  std::to_string(hinfo) + ")");
@@ -1901,12 +2200,12 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
       F.ldV = pad4(r);
       {
         std::lock_guard<std::mutex> g(mtx);
-        F.A64 = c->dalloc<double>((size_t)r * F.ldA);
-        F.A32 = c->dalloc<float>((size_t)r * F.ldA);
-        F.V64 = c->dalloc<double>((size_t)ncol * F.ldV);
-        F.V32 = c->dalloc<float>((size_t)ncol * F.ldV);
-        F.A2 = c->dalloc<float2>((size_t)r * F.ldA);
-        F.V2 = c->dalloc<float2>((size_t)ncol * F.ldV);
+        F.A64 = (double*)falloc(sizeof(double) * (size_t)r * F.ldA);
+        F.A32 = (float*)falloc(sizeof(float) * (size_t)r * F.ldA);
+        F.V64 = (double*)falloc(sizeof(double) * (size_t)ncol * F.ldV);
+        F.V32 = (float*)falloc(sizeof(float) * (size_t)ncol * F.ldV);
+        F.A2 = (float2*)falloc(sizeof(float2) * (size_t)r * F.ldA);
+        F.V2 = (float2*)falloc(sizeof(float2) * (size_t)ncol * F.ldV);
       }
       if (!F.A64 || !F.A32 || !F.V64 || !F.V32 || !F.A2 || !F.V2) {
         fail_w(MFS_ERR_OOM, "device allocation failed: one-body factors");
@@ -1920,7 +2219,7 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
         F.ldQ = pad4(m);
         {
           std::lock_guard<std::mutex> g(mtx);
-          F.Q32 = c->dalloc<float>((size_t)3 * n_eq * F.ldQ);
+          F.Q32 = (float*)falloc(sizeof(float) * (size_t)3 * n_eq * F.ldQ);
         }
         if (!F.Q32) {
           fail_w(MFS_ERR_OOM, "device allocation failed: far-field matrices");
@@ -1949,6 +2248,12 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
         break;
       }
       c->factors[f] = F;
+      if (ent) {
+        ent->F = F;
+        store_add(ent);
+        std::lock_guard<std::mutex> g(mtx);
+        c->shared.push_back(ent);
+      }
     }
     cleanup();
   };
@@ -2110,15 +2415,21 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
     if (nf > 0 && p.tensor_step1 != 0 && (int)tck.size() >= tc_min) {
       const Factor& F = c->factors[shared_f];
       const int ldk = tc_ldk(F.m), ncap = (int)tck.size();
-      void* as[3];
+      // the factor of spheres without images lives in the store, with its bf16 slices
+      SharedFactor* se = nullptr;
+      for (auto& e : c->shared)
+        if (e->F.A64 == F.A64) se = e.get();
+      if (!se) return c->fail(MFS_ERR_STATE, "tensor-core step 1: the shared factor is not in the store");
+      if ((s = ensure_tc_slices(c, *se)) != MFS_OK) return s;
+      if (c->mem_limit && c->mem_used + se->tc_bytes > c->mem_limit)
+        return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices (memory cap)");
+      c->mem_used += se->tc_bytes;
       void* xs[3];
       for (int i = 0; i < 3; ++i) {
-        as[i] = c->dalloc<uint16_t>((size_t)F.rank * ldk);
         xs[i] = c->dalloc<uint16_t>((size_t)ncap * ldk);
-        if (!as[i] || !xs[i]) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
+        if (!xs[i]) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
       }
-      launch_split3_matrix(F.rank, F.m, F.ldA, F.A64, ldk, as[0], as[1], as[2], c->stream);
-      if (!tc_prepare(c->tcA, as, F.rank, xs, ncap, F.m))
+      if (!tc_prepare(c->tcA, se->as, F.rank, xs, ncap, F.m))
         return c->fail(MFS_ERR_CUDA, "tensor-core step 1: tensor maps or shared-memory limit unavailable");
       size_t part = tc_partial_floats(c->tcA, ncap);
       std::vector<long long> xo(ncap), ya(ncap), yq(ncap);
@@ -2129,13 +2440,7 @@ static mfs_status build_impl(mfs_ctx* c, const mfs_params* params) {
         yq[i] = 3LL * n_eq * k;
       }
       if (far_on) {
-        void* qs[3];
-        for (int i = 0; i < 3; ++i) {
-          qs[i] = c->dalloc<uint16_t>((size_t)3 * n_eq * ldk);
-          if (!qs[i]) return c->fail(MFS_ERR_OOM, "device allocation failed: tensor-core slices");
-        }
-        launch_split3_matrix_f32(3 * n_eq, F.m, F.ldQ, F.Q32, ldk, qs[0], qs[1], qs[2], c->stream);
-        if (!tc_prepare(c->tcQ, qs, 3 * n_eq, xs, ncap, F.m))
+        if (!tc_prepare(c->tcQ, se->qs, 3 * n_eq, xs, ncap, F.m))
           return c->fail(MFS_ERR_CUDA, "tensor-core step 1: tensor maps unavailable");
         part = std::max(part, tc_partial_floats(c->tcQ, ncap));
         if ((s = upload(c, c->d_tc_yQ, yq)) != MFS_OK) return s;
@@ -2310,6 +2615,8 @@ mfs_status mfs_sizes(const mfs_ctx* cc, mfs_sizes_t* out) {
   out->pairs_fp = pairs;
   out->pairs_near_fp = c->ff.n_eq > 0 ? c->near_pairs_per_apply : pairs;
   out->pairs_far_eq = c->ff.n_eq > 0 ? c->far_pairs_per_apply : 0;
+  out->n_factors_shared = (int)c->shared.size();
+  out->n_factors_reused = c->factors_reused;
   return MFS_OK;
 }
 

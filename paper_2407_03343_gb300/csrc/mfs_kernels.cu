@@ -22,6 +22,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "mfs_internal.h"
 
@@ -1730,15 +1733,33 @@ void launch_pairs_dw(const TargetSet& tg, const SourceSet& src, const double* la
   }
 }
 
-// source parts per tile so that tiles x parts fill whole waves of the resident CTAs (ties: fewer)
-int wave_parts(long long tiles, const void* kernel, int max_parts) {
-  int per_sm = 0, sms = 0, dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+// resident CTAs of a pair kernel on the current device (SMs x CTAs per SM), looked up once per
+// (device, kernel)
+static double resident_ctas(const void* kernel) {
+  static std::mutex mtx;
+  static std::vector<std::pair<std::pair<int, const void*>, double>> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> g(mtx);
+  for (const auto& e : cache)
+    if (e.first.first == dev && e.first.second == kernel) return e.second;
+  int per_sm = 0, sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPairThreads, 0) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
-    return 1;
+    return 0;
   }
-  const double wave = (double)sms * per_sm;
+  cache.push_back({{dev, kernel}, (double)sms * per_sm});
+  return cache.back().second;
+}
+
+// source parts per tile so that tiles x parts fill whole waves of the resident CTAs (ties: fewer)
+int wave_parts(long long tiles, const void* kernel, int max_parts) {
+  const double wave = resident_ctas(kernel);
+  if (wave <= 0) return 1;
   int best = 1;
   double best_eff = 0;
   for (int p = 1; p <= max_parts; ++p) {

@@ -27,7 +27,6 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "mfs_internal.h"
 
@@ -361,12 +360,12 @@ bool tc_prepare(TcGemm& g, const void* const a_slices[3], int M, const void* con
   g.x_slices[0] = const_cast<void*>(x_slices[0]);
   g.x_slices[1] = const_cast<void*>(x_slices[1]);
   g.x_slices[2] = const_cast<void*>(x_slices[2]);
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-  });
-  return attr == cudaSuccess;
+  // the shared-memory limit is a per-device attribute of the kernel: set it on the current device
+  if (cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
 }
 
 // K-ranges per tile so that the grid covers about one wave of the 152 SMs

@@ -56,7 +56,7 @@ class Sizes(C.Structure):
     _fields_ = [("P", C.c_int), ("n_contacts", C.c_int), ("n_colloc", C.c_int),
                 ("n_proxy_total", C.c_int), ("n_image_nodes", C.c_int), ("n_unknowns", C.c_int),
                 ("n_factors", C.c_int), ("pairs_fp", C.c_longlong), ("pairs_near_fp", C.c_longlong),
-                ("pairs_far_eq", C.c_longlong)]
+                ("pairs_far_eq", C.c_longlong), ("n_factors_shared", C.c_int), ("n_factors_reused", C.c_int)]
 
 
 class Timing(C.Structure):
@@ -67,7 +67,8 @@ class Timing(C.Structure):
                 ("by_kind_launches", C.c_longlong * 3), ("by_kind_ms", C.c_double * 3),
                 ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3),
                 ("krylov_launches", C.c_longlong), ("krylov_ms", C.c_double), ("krylov_bytes", C.c_double),
-                ("far_launches", C.c_longlong), ("far_ms", C.c_double), ("far_pairs", C.c_longlong)]
+                ("far_launches", C.c_longlong), ("far_ms", C.c_double), ("far_pairs", C.c_longlong),
+                ("tc_launches", C.c_longlong), ("tc_columns", C.c_longlong)]
 
 
 class PairShapes(C.Structure):
