@@ -1450,14 +1450,19 @@ __global__ void axpy64_kernel(long long n, double a, const double* __restrict__ 
 // right-hand side g rotated and the residual estimate |g_{j+1}| / ||b|| updated.  A problem that
 // meets its tolerance (or breaks down) is deactivated here, on the device, so the host need
 // not wait for every step; scl = 1 / h_{j+1,j} normalises the new basis vector.
-// One CTA per problem: the column and the rotations are staged in shared memory in parallel,
-// one thread runs the sequential rotation chain there, and the column is written back.
+// One CTA per problem.  Applying the earlier rotations to the new column is the first-order
+// linear recurrence r_{i+1} = -sn_i r_i + cs_i h_{i+1} (r_0 = h_0) with outputs
+// h'_i = cs_i r_i + sn_i h_{i+1}; the CTA evaluates it as a parallel prefix of the affine maps
+// r -> a r + b (each thread composes a contiguous run, a warp scan and the warp totals give every
+// run its starting r), so its FP64 work is a few dependent operations per thread instead of a
+// chain of j on one thread.
 __global__ void batch_givens_kernel(GivensState S, int j, const double* __restrict__ h1, const double* __restrict__ h2,
                                     const double* __restrict__ hn) {
   const int p = blockIdx.x;
   if (!S.active[p]) return;
   __shared__ double col[kMaxGmresCol + 1], cs[kMaxGmresCol], sn[kMaxGmresCol];
-  __shared__ int done;
+  __shared__ double wa[32], wb[32], rj, hnext;
+  __shared__ int bad;
   double* colg = S.H + ((long long)p * S.restart + j) * S.ldh;
   double* csg = S.cs + (long long)p * S.restart;
   double* sng = S.sn + (long long)p * S.restart;
@@ -1467,43 +1472,78 @@ __global__ void batch_givens_kernel(GivensState S, int j, const double* __restri
     cs[i] = csg[i];
     sn[i] = sng[i];
   }
-  __syncthreads();
   if (threadIdx.x == 0) {
-    done = 0;
-    const double hnext = sqrt(fmax(0.0, hn[p]));
-    if (!isfinite(hnext)) {
-      S.err[0] = 1;
-      S.active[p] = 0;
-      done = 1;
-    } else {
-      // earlier rotations; r carries the partly rotated entry down the column, so the dependent
-      // chain is one multiply-add per step while the loads of h, cs and sn run ahead of it
-      double r = col[0];
-      for (int i = 0; i < j; ++i) {
-        const double x = col[i + 1];
-        col[i] = cs[i] * r + sn[i] * x;
-        r = -sn[i] * r + cs[i] * x;
-      }
-      col[j] = r;
-      col[j + 1] = hnext;
-      const double den = hypot(col[j], col[j + 1]);
-      const double c = den > 0 ? col[j] / den : 1.0, sj = den > 0 ? col[j + 1] / den : 0.0;
-      csg[j] = c;
-      sng[j] = sj;
-      col[j] = den;
-      col[j + 1] = 0.0;
-      g[j + 1] = -sj * g[j];
-      g[j] = c * g[j];
-      S.jused[p] = j + 1;
-      S.iters[p] += 1;
-      S.est[p] = fabs(g[j + 1]) / S.bn[p];
-      S.scl[p] = hnext > 0 ? 1.0 / hnext : 0.0;
-      if (S.est[p] <= S.tol[p] || hnext == 0.0) S.active[p] = 0;
-    }
+    hnext = sqrt(fmax(0.0, hn[p]));
+    bad = !isfinite(hnext);
+    if (j == 0) rj = 0.0;
   }
   __syncthreads();
-  if (done) return;
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) colg[i] = col[i];
+  if (bad) {
+    if (threadIdx.x == 0) {
+      S.err[0] = 1;
+      S.active[p] = 0;
+    }
+    return;
+  }
+  // this thread's run [i0, i1) of the rotations, composed into r -> A r + B
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (j + blockDim.x - 1) / blockDim.x;
+  const int i0 = min(j, tid * per), i1 = min(j, i0 + per);
+  double A = 1.0, B = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    const double a = -sn[i];
+    B = fma(a, B, cs[i] * col[i + 1]);
+    A *= a;
+  }
+  // inclusive scan over the warp's runs (a later run applies after an earlier one)
+  for (int o = 1; o < 32; o <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, o), Bp = __shfl_up_sync(0xffffffffu, B, o);
+    if (lane >= o) {
+      B = fma(A, Bp, B);
+      A *= Ap;
+    }
+  }
+  if (lane == 31) {
+    wa[warp] = A;
+    wb[warp] = B;
+  }
+  __syncthreads();
+  // the composition of every run before this thread's: the earlier warps', then the earlier lanes'
+  double PA = 1.0, PB = 0.0;
+  for (int q = 0; q < warp; ++q) {
+    PB = fma(wa[q], PB, wb[q]);
+    PA *= wa[q];
+  }
+  double EA = __shfl_up_sync(0xffffffffu, A, 1), EB = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) {
+    EA = 1.0;
+    EB = 0.0;
+  }
+  double r = fma(EA, fma(PA, col[0], PB), EB);  // r at i0
+  for (int i = i0; i < i1; ++i) {
+    const double x = col[i + 1];
+    colg[i] = fma(cs[i], r, sn[i] * x);
+    r = fma(-sn[i], r, cs[i] * x);
+  }
+  if (i1 == j && i0 < i1) rj = r;
+  if (j == 0 && tid == 0) rj = col[0];
+  __syncthreads();
+  if (tid == 0) {
+    const double cj = rj, hx = hnext;
+    const double den = hypot(cj, hx);
+    const double c = den > 0 ? cj / den : 1.0, sj = den > 0 ? hx / den : 0.0;
+    csg[j] = c;
+    sng[j] = sj;
+    colg[j] = den;
+    colg[j + 1] = 0.0;
+    g[j + 1] = -sj * g[j];
+    g[j] = c * g[j];
+    S.jused[p] = j + 1;
+    S.iters[p] += 1;
+    S.est[p] = fabs(g[j + 1]) / S.bn[p];
+    S.scl[p] = hx > 0 ? 1.0 / hx : 0.0;
+    if (S.est[p] <= S.tol[p] || hx == 0.0) S.active[p] = 0;
+  }
 }
 
 // y = R^{-1} g per problem (back substitution over its own jused steps): coef[i K + p] = y_i,
