@@ -1006,7 +1006,9 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
          cudaMallocHost(&B->jpin_rest, sizeof(int) * std::max<size_t>(1, jp.size())) == cudaSuccess;
   }
   // vector chunks, each inside one problem
-  const long long chunk = 1024;  // enough chunks to fill the GPU for batches of small problems
+  // 1024-element chunks: enough CTAs for batches of small problems (256 was measured slower: the
+  // per-CTA coefficient loads and the per-problem reduction grow with the chunk count)
+  const long long chunk = 1024;
   std::vector<int> cprob, pchunk(1, 0);
   std::vector<long long> cs, ce;
   for (int p = 0; p < K; ++p) {
@@ -1025,6 +1027,7 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
   if (ok) {
     B->seg.K = K;
     B->seg.nchunks = (int)cprob.size();
+    B->seg.chunk = (int)chunk;
     B->seg.prob = dcp;
     B->seg.start = dcs;
     B->seg.end = dce;

@@ -248,6 +248,7 @@ void launch_sub(int n, const double* a, const double* b, double* out, cudaStream
 // vector-major, c[i * K + p].  Chunks of inactive problems do nothing.
 struct SegTable {
   int K = 0, nchunks = 0;
+  int chunk = 1024;             // longest chunk (at most 1024 elements)
   const int* prob = nullptr;
   const long long* start = nullptr;
   const long long* end = nullptr;

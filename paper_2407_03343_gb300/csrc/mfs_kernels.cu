@@ -1369,13 +1369,26 @@ __global__ void seg_dots_kernel(SegTable t, int nvec, const double* __restrict__
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int i1 = min(nvec, (int)(blockIdx.y + 1) * kSegDotVecs);
-  for (int i = blockIdx.y * kSegDotVecs + warp; i < i1; i += nwarps) {
+  // two vectors per warp at a time, so that twice the loads are in flight
+  for (int i = blockIdx.y * kSegDotVecs + warp; i < i1; i += 2 * nwarps) {
+    const int i2 = i + nwarps;
     const double* v = V + (long long)i * ldv + lo;
-    double d = 0.0;
+    const double* v2 = V + (long long)min(i2, i1 - 1) * ldv + lo;
+    double d = 0.0, d2 = 0.0;
 #pragma unroll 8
-    for (int e = lane; e < len; e += 32) d += v[e] * ws[e];
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (lane == 0) partial[(long long)i * t.nchunks + b] = d;
+    for (int e = lane; e < len; e += 32) {
+      const double x = ws[e];
+      d += v[e] * x;
+      d2 += v2[e] * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    }
+    if (lane == 0) {
+      partial[(long long)i * t.nchunks + b] = d;
+      if (i2 < i1) partial[(long long)i2 * t.nchunks + b] = d2;
+    }
   }
   if (!t.counter) return;
   // the last CTA of problem p to finish adds its partial dots in chunk order (so the result does
@@ -1409,22 +1422,36 @@ __global__ void seg_reduce_kernel(SegTable t, int nvec, const double* __restrict
   }
 }
 
-// w += sign * sum_i coef[i K + p] V_i over one kSegUpdSub-element piece of a chunk per CTA
-__global__ void seg_update_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
-                                  const double* __restrict__ coef, double sign, double* __restrict__ w) {
+// w += sign * sum_i coef[i K + p] V_i over one kSegUpdSub-element piece of a chunk per CTA.  The
+// CTA's kSegUpdGroups thread groups take interleaved vectors (more loads in flight when a short
+// problem has few pieces) and their sums are added in group order.
+constexpr int kSegUpdGroups = 4;
+__global__ void __launch_bounds__(kSegUpdSub* kSegUpdGroups)
+    seg_update_kernel(SegTable t, int nvec, const double* __restrict__ V, long long ldv,
+                      const double* __restrict__ coef, double sign, double* __restrict__ w) {
   const int b = seg_chunk(t);
   const int p = t.prob[b];
   if (!t.active[p]) return;
-  const long long e = t.start[b] + (long long)blockIdx.y * kSegUpdSub + threadIdx.x;
+  const int tl = threadIdx.x % kSegUpdSub, g = threadIdx.x / kSegUpdSub;
+  const long long e = t.start[b] + (long long)blockIdx.y * kSegUpdSub + tl;
   if (t.start[b] + (long long)blockIdx.y * kSegUpdSub >= t.end[b]) return;  // whole CTA past the chunk
   __shared__ double c[512];
+  __shared__ double red[kSegUpdGroups][kSegUpdSub];
   for (int i = threadIdx.x; i < nvec; i += blockDim.x) c[i] = sign * coef[(long long)i * t.K + p];
   __syncthreads();
-  if (e >= t.end[b]) return;
-  double a = w[e];
+  double a = 0.0;
+  if (e < t.end[b]) {
 #pragma unroll 8
-  for (int i = 0; i < nvec; ++i) a += c[i] * V[(long long)i * ldv + e];
-  w[e] = a;
+    for (int i = g; i < nvec; i += kSegUpdGroups) a += c[i] * V[(long long)i * ldv + e];
+  }
+  red[g][tl] = a;
+  __syncthreads();
+  if (g == 0 && e < t.end[b]) {
+    double s = w[e];
+#pragma unroll
+    for (int q = 0; q < kSegUpdGroups; ++q) s += red[q][tl];
+    w[e] = s;
+  }
 }
 
 inline int seg_ctas(const SegTable& t) { return t.list ? t.nlist : t.nchunks; }
@@ -1916,7 +1943,7 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
       if (parts > 1) {
         ++t_launches;
         if (seg_ctas(seg) > 0)
-          pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), kSegChunkMax / 128), 128, 0, st>>>(seg, args, bv, parts);
+          pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), (seg.chunk + 127) / 128), 128, 0, st>>>(seg, args, bv, parts);
       }
     }
   } else {
@@ -1940,7 +1967,8 @@ void launch_seg_update(const SegTable& t, int nvec, const double* V, long long l
                        double* w, cudaStream_t st) {
   if (seg_ctas(t) == 0 || nvec == 0) return;
   ++t_launches;
-  seg_update_kernel<<<dim3(seg_ctas(t), kSegChunkMax / kSegUpdSub), kSegUpdSub, 0, st>>>(t, nvec, V, ldv, coef, sign, w);
+  seg_update_kernel<<<dim3(seg_ctas(t), (t.chunk + kSegUpdSub - 1) / kSegUpdSub), kSegUpdSub * kSegUpdGroups, 0, st>>>(
+      t, nvec, V, ldv, coef, sign, w);
 }
 void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st) {
   if (seg_ctas(t) == 0) return;
