@@ -363,6 +363,13 @@ typedef struct {
    * sphere columns they covered */
   long long tc_launches;
   long long tc_columns;
+  /* FP32-pipe flops issued by the double-float pair evaluations: 248 per (node, proxy) pair and
+   * 544 per (node, image node) triple for one right-hand side; in a batch, the right-hand sides on
+   * one geometry (R of them) share each pair's geometry (distance and its powers: 99 and 106
+   * flops), so such a pair issues 99 + 149 R (triple: 106 + 438 R).  pair_shared_rhs counts the
+   * pair_interactions evaluated that way. */
+  double pair_issued_flops;
+  long long pair_shared_rhs;
 } mfs_timing_t;
 mfs_status mfs_set_profiling(mfs_ctx* ctx, int on);
 /* Copies the counters; reset != 0 zeroes them afterwards. */

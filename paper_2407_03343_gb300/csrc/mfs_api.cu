@@ -37,6 +37,12 @@ constexpr double kPi = 3.14159265358979323846;
 
 inline int pad4(int x) { return (x + 3) & ~3; }
 
+// FP32-pipe flops of the compensated double-float pair evaluation (counted from the kernel's
+// operations, FMA = 2): a Stokeslet pair's geometry (differences, distance, 1/r, 1/r^2) and its
+// per-right-hand-side part; an image triple's geometry (with 1/r^3) and its S + R + D part
+constexpr double kDwPairGeomFlops = 99.0, kDwPairRhsFlops = 149.0;
+constexpr double kDwTripleGeomFlops = 106.0, kDwTripleRhsFlops = 438.0;
+
 struct Factor {
   int m = 0, ncol = 0, rank = 0, ldA = 0, ldV = 0;
   double* A64 = nullptr;  // rank x ldA  (Sigma^+ U^T)
@@ -444,6 +450,8 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
       });
       c->tm.pair_launches += 1;
       c->tm.pair_interactions += c->near_pairs_per_apply;
+      c->tm.pair_issued_flops += (double)c->near_proxy_per_apply * (kDwPairGeomFlops + kDwPairRhsFlops) +
+                                 (double)c->near_image_per_apply * (kDwTripleGeomFlops + kDwTripleRhsFlops);
       c->tm.pair_proxy += c->near_proxy_per_apply;
       c->tm.pair_image_nodes += c->near_image_per_apply;
       c->tm.pair_kind = MFS_MIXED;
@@ -468,6 +476,9 @@ void pairs_step(mfs_ctx* c, const T* lam_hat, const T* mu, T* out) {
   });
   c->tm.pair_launches += 1;
   c->tm.pair_interactions += c->pairs_per_apply;
+  if (sizeof(T) == 8 && c->dw_pairs)
+    c->tm.pair_issued_flops += (double)c->proxy_per_apply * (kDwPairGeomFlops + kDwPairRhsFlops) +
+                               (double)c->image_per_apply * (kDwTripleGeomFlops + kDwTripleRhsFlops);
   c->tm.pair_proxy += c->proxy_per_apply;
   c->tm.pair_image_nodes += c->image_per_apply;
   c->tm.pair_kind = sizeof(T) == 4 ? MFS_FP32 : (c->dw_pairs ? MFS_MIXED : MFS_FP64);
@@ -747,6 +758,18 @@ struct BatchPlan {
   float* tc_partial = nullptr;
   int* tc_err = nullptr;
   std::vector<char> jtc_host;              // per GEMV job: 1 when it is a tensor column
+  // several right-hand sides on one geometry in one pair-kernel pass (double-float): items
+  // (lead problem, tile, first index into the right-hand-side list, count) and the 128-node
+  // tiles of the problems left single
+  int4* d_mwork = nullptr;
+  int4* mwork_pin = nullptr;
+  int* d_rhs = nullptr;
+  int* rhs_pin = nullptr;
+  int2* d_swork1 = nullptr;
+  int2* swork_pin = nullptr;
+  int n_mwork = 0, n_swork1 = 0;
+  size_t mwork_cap = 0;
+  std::vector<int> rhs_shared;             // per problem: right-hand sides in its pair-kernel item
   std::vector<int> leader;                 // per problem: the first problem on the same context
   std::vector<double> bA32_p, bA2_p, bV_p; // per context (at its leader): factor bytes of one step 1
   int* d_jlist_rest = nullptr;             // compacted list of the active problems' other jobs
@@ -771,6 +794,9 @@ struct BatchPlan {
     if (cpin) cudaFreeHost(cpin);
     if (jpin) cudaFreeHost(jpin);
     if (tc_pin) cudaFreeHost(tc_pin);
+    if (mwork_pin) cudaFreeHost(mwork_pin);
+    if (rhs_pin) cudaFreeHost(rhs_pin);
+    if (swork_pin) cudaFreeHost(swork_pin);
     if (jpin_rest) cudaFreeHost(jpin_rest);
     if (snap) cudaFreeHost(snap);
     for (void* q : gs_allocs) cudaFree(q);
@@ -975,6 +1001,12 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
     B->gA32.y_off = dyA; B->gA32.n_jobs = (int)mA32.size(); B->gA32.max_rows = maxA; B->gA32.job_prob = djp;
     B->gA32.active = B->d_active;
   }
+  B->mwork_cap = std::max<size_t>(1, B->w1_host.size());
+  ok = ok && (B->d_mwork = B->alloc<int4>(B->mwork_cap)) && (B->d_rhs = B->alloc<int>(K)) &&
+       (B->d_swork1 = B->alloc<int2>(B->mwork_cap)) &&
+       cudaMallocHost(&B->mwork_pin, sizeof(int4) * B->mwork_cap) == cudaSuccess &&
+       cudaMallocHost(&B->rhs_pin, sizeof(int) * K) == cudaSuccess &&
+       cudaMallocHost(&B->swork_pin, sizeof(int2) * B->mwork_cap) == cudaSuccess;
   if (ok && best) {
     const Factor& F = best->F;
     const int ncap = (int)B->tc_prob.size();
@@ -1096,6 +1128,41 @@ mfs_status set_active(BatchRun& R, const std::vector<int>& a) {
     if (a[w.x]) w1[n1++] = w;
   B->n_cwork = n4;
   B->n_cwork1 = n1;
+  // the active problems of a context in chunks of up to kPairRhs: a chunk of two or more shares
+  // the pair kernel's work items, a problem alone keeps the single-problem kernel
+  {
+    int nm = 0, nr = 0, ns = 0;
+    std::vector<char> single(B->K, 0);
+    B->rhs_shared.assign(B->K, 1);
+    for (int L = 0; L < B->K; ++L) {
+      if (B->leader[L] != L) continue;
+      std::vector<int> mem;
+      for (int p = L; p < B->K; ++p)
+        if (B->leader[p] == L && a[p]) mem.push_back(p);
+      for (size_t c0 = 0; c0 < mem.size(); c0 += kPairRhs) {
+        const int cnt = (int)std::min<size_t>(kPairRhs, mem.size() - c0);
+        if (cnt == 1) {
+          single[mem[c0]] = 1;
+          continue;
+        }
+        const int r0 = nr;
+        for (int q = 0; q < cnt; ++q) {
+          B->rhs_pin[nr++] = mem[c0 + q];
+          B->rhs_shared[mem[c0 + q]] = cnt;
+        }
+        for (int t = 0; t < B->tiles1[L]; ++t) B->mwork_pin[nm++] = make_int4(L, t, r0, cnt);
+      }
+    }
+    for (const int2& w : B->w1_host)
+      if (single[w.x]) B->swork_pin[ns++] = w;
+    B->n_mwork = nm;
+    B->n_swork1 = ns;
+    if (nm) {
+      CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_mwork, B->mwork_pin, sizeof(int4) * nm, cudaMemcpyHostToDevice, R.st));
+      CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_rhs, B->rhs_pin, sizeof(int) * nr, cudaMemcpyHostToDevice, R.st));
+    }
+    if (ns) CUDA_TRY(R.c0, cudaMemcpyAsync(B->d_swork1, B->swork_pin, sizeof(int2) * ns, cudaMemcpyHostToDevice, R.st));
+  }
   int nc = 0;
   for (int b = 0; b < (int)B->cprob_host.size(); ++b)
     if (a[B->cprob_host[b]]) B->cpin[nc++] = b;
@@ -1176,7 +1243,18 @@ void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
   // few tiles left (the lockstep tail): split each tile's sources over several CTAs
   const int parts = R.dw && nt == 1 && min_others > 0 ? pair_split_parts(B->n_cwork1, min_others, kPairMaxParts) : 1;
   timed(c, c->ev_pair, [&] {
-    if (nt == 4)
+    if (R.dw && B->n_mwork > 0) {
+      // right-hand sides on one geometry share the pair evaluations; the problems left single
+      // run the 1-node-per-thread kernel with the same source split, one reduction for both
+      const long long items = (long long)B->n_mwork + B->n_swork1;
+      const int mparts = min_others > 0 ? pair_split_parts(items, min_others, kPairMaxParts) : 1;
+      launch_pairs_multi64(B->d_args1, B->d_mwork, B->n_mwork, B->d_rhs, B->d_active, B->lh, in, out, B->d_uoff,
+                           B->d_voff, mparts, B->pparts, B->n_total, B->d_nlen, R.st);
+      launch_pairs_batch64(true, B->d_args1, B->d_swork1, B->n_swork1, B->d_active, 1, B->lh, in, out, B->d_uoff,
+                           B->d_voff, mparts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen, true);
+      launch_pair_parts_reduce_batch(B->d_args1, B->seg, B->lh, in, out, B->d_uoff, B->d_voff, mparts, B->pparts,
+                                     B->n_total, B->d_nlen, R.st);
+    } else if (nt == 4)
       launch_pairs_batch64(R.dw, B->d_args, B->d_cwork, B->n_cwork, B->d_active, 4, B->lh, in, out, B->d_uoff,
                            B->d_voff, 1, nullptr, 0, B->seg, R.st);
     else
@@ -1210,6 +1288,13 @@ void batch_apply_count(BatchRun& R, const std::vector<int>& act) {
   std::vector<int> per_ctx(B->K, 0);
   for (int p = 0; p < B->K; ++p)
     if (act[p]) {
+      if (R.dw) {
+        // a geometry shared by r right-hand sides is evaluated once for all of them
+        const int r = B->n_mwork > 0 && (int)B->rhs_shared.size() == B->K ? B->rhs_shared[p] : 1;
+        c->tm.pair_issued_flops += (double)B->proxy_p[p] * (kDwPairRhsFlops + kDwPairGeomFlops / r) +
+                                   (double)B->image_p[p] * (kDwTripleRhsFlops + kDwTripleGeomFlops / r);
+        if (r > 1) c->tm.pair_shared_rhs += B->pairs_p[p];
+      }
       c->tm.pair_interactions += B->pairs_p[p];
       c->tm.pair_proxy += B->proxy_p[p];
       c->tm.pair_image_nodes += B->image_p[p];

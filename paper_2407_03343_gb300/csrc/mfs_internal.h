@@ -187,7 +187,20 @@ struct SegTable;
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
-                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen = nullptr);
+                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen = nullptr,
+                          bool skip_reduce = false);
+// Several right-hand sides on one geometry (double-float, 1 node per thread): work[b] = (lead
+// problem, tile, first index into rhs_prob, count <= kPairRhs); each pair's Green's function is
+// formed once for all of the item's right-hand sides.  parts > 1 writes partial sums as
+// launch_pairs_batch64 does; the caller then runs launch_pair_parts_reduce_batch once.
+constexpr int kPairRhs = 3;
+void launch_pairs_multi64(const void* d_args1, const int4* d_work, int n_work, const int* d_rhs, const int* d_active,
+                          const double* lam, const double* mu, double* out, const long long* d_uoff,
+                          const long long* d_voff, int parts, double* partial, long long pstride,
+                          const long long* d_nlen, cudaStream_t st);
+void launch_pair_parts_reduce_batch(const void* d_args1, const SegTable& seg, const double* lam, const double* mu,
+                                    double* out, const long long* d_uoff, const long long* d_voff, int parts,
+                                    double* partial, long long pstride, const long long* d_nlen, cudaStream_t st);
 
 // Batched GEMV: for every job j, y_j = M_j x_j with M_j row-major (rows_j x cols_j, leading dim ld_j).
 template <typename T>

@@ -1044,6 +1044,255 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const Pair
   A.out = bv.out + bv.voff[w.x];
   pair_tile_dw<NT>(A, w.y, blockIdx.x % nparts, nparts, bv.partial + bv.voff[w.x], bv.pstride);
 }
+// ------------------------------------------------------------------ several right-hand sides on one geometry
+// The problems of a batch that share a context (the motions of one geometry) have the same
+// targets and sources and differ only in their strengths.  Work item (lead problem, 128-node
+// tile, first index into the right-hand-side list, count <= kPairRhs): the position
+// differences, the distance and its powers of each (node, source) pair are formed once in
+// double-float and applied to the strengths of every listed right-hand side (~85 of the ~204
+// FP32 operations of a Stokeslet pair, ~89 of ~436 of an image triple, are shared).  Each
+// right-hand side's sums follow the operation order of pair_tile_dw.
+constexpr int kTileProxyM = 128;  // proxy sources staged per round
+constexpr int kTileImgM = 64;     // image nodes staged per round
+
+template <int R>
+struct DWMulti {
+  dw x, y, z;
+  dw ux[R], uy[R], uz[R];
+};
+
+template <int R>
+__device__ __forceinline__ void dwm_proxy_range(const PairArgs<double>& A, const CentreShift64& sh, int k,
+                                                const double* const (&lam)[R], unsigned mask, int r_lo, int r_hi,
+                                                float4* sp, float4 (*sf)[2 * kTileProxyM], DWMulti<R>& T) {
+  const double far = 1e18;
+  const int total = A.P * A.N;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileProxyM) {
+    const int ns = min(kTileProxyM, r_hi - s0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
+      const int j = s0 + i;
+      double px = far, py = far, pz = far;
+      int o = -1, jj = 0;
+      if (j < total) {
+        o = j / A.N;
+        jj = j - o * A.N;
+        const D4 pr = A.proxy[jj];
+        px = pr.x + sh.d(o, 0);
+        py = pr.y + sh.d(o, 1);
+        pz = pr.z + sh.d(o, 2);
+      }
+      dw a = dw_split(px), b = dw_split(py), c = dw_split(pz);
+      sp[2 * i] = make_float4(a.h, b.h, c.h, 0.f);
+      sp[2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        double fx = 0, fy = 0, fz = 0;
+        if ((mask >> r & 1u) && o >= 0 && o != k) {
+          const double* l = lam[r] + A.unk_off[o] + 3LL * jj;
+          fx = l[0];
+          fy = l[1];
+          fz = l[2];
+        }
+        a = dw_split(fx);
+        b = dw_split(fy);
+        c = dw_split(fz);
+        sf[r][2 * i] = make_float4(a.h, b.h, c.h, 0.f);
+        sf[r][2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < ns; ++j) {
+      const float4 ph = sp[2 * j], pl = sp[2 * j + 1];
+      const dw dx = sub_pos(T.x, dw{ph.x, pl.x});
+      const dw dy = sub_pos(T.y, dw{ph.y, pl.y});
+      const dw dz = sub_pos(T.z, dw{ph.z, pl.z});
+      const dw ir = rsqrt_u(norm2_u(dx, dy, dz));
+      const dw ir2 = mul_u(ir, ir);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!(mask >> r & 1u)) continue;
+        const float4 fh = sf[r][2 * j], fl = sf[r][2 * j + 1];
+        const dw fx{fh.x, fl.x}, fy{fh.y, fl.y}, fz{fh.z, fl.z};
+        const dw c = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
+        acc_u(T.ux[r], mul_u(ir, add_u(fx, mul_u(c, dx))));
+        acc_u(T.uy[r], mul_u(ir, add_u(fy, mul_u(c, dy))));
+        acc_u(T.uz[r], mul_u(ir, add_u(fz, mul_u(c, dz))));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T.ux[r] = two_sum(T.ux[r].h, T.ux[r].l);
+      T.uy[r] = two_sum(T.uy[r].h, T.uy[r].l);
+      T.uz[r] = two_sum(T.uz[r].h, T.uz[r].l);
+    }
+  }
+}
+
+// image node strengths of one right-hand side in 5 float4: hi of (f, t, d) then lo of the same
+template <int R>
+__device__ __forceinline__ void dwm_image_range(const PairArgs<double>& A, const CentreShift64& sh, int k,
+                                                const double* const (&lam)[R], unsigned mask, int r_lo, int r_hi,
+                                                float4* sip, float4 (*sis)[5 * kTileImgM], DWMulti<R>& T) {
+  const double far = 1e18;
+  for (int s0 = r_lo; s0 < r_hi; s0 += kTileImgM) {
+    const int ns = min(kTileImgM, r_hi - s0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < ns; i += kPairThreads) {
+      const int j = s0 + i;
+      double px = far, py = far, pz = far;
+      int o = -1;
+      if (j < A.n_img) {
+        o = A.img_owner[j];
+        const D4 pr = A.img[j];
+        px = pr.x + sh.d(o, 0);
+        py = pr.y + sh.d(o, 1);
+        pz = pr.z + sh.d(o, 2);
+      }
+      dw a = dw_split(px), b = dw_split(py), c = dw_split(pz);
+      sip[2 * i] = make_float4(a.h, b.h, c.h, 0.f);
+      sip[2 * i + 1] = make_float4(a.l, b.l, c.l, 0.f);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float hv[9], lv[9];
+        const double* l = nullptr;
+        if ((mask >> r & 1u) && o >= 0 && o != k) l = lam[r] + A.unk_off[o] + 3LL * A.N + 9LL * (j - A.img_off[o]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const double v = l ? (q < 6 ? l[q] : A.dip * l[q]) : 0.0;
+          const dw sv = dw_split(v);
+          hv[q] = sv.h;
+          lv[q] = sv.l;
+        }
+        sis[r][5 * i] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        sis[r][5 * i + 1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        sis[r][5 * i + 2] = make_float4(hv[8], lv[0], lv[1], lv[2]);
+        sis[r][5 * i + 3] = make_float4(lv[3], lv[4], lv[5], lv[6]);
+        sis[r][5 * i + 4] = make_float4(lv[7], lv[8], 0.f, 0.f);
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < ns; ++j) {
+      const float4 ph = sip[2 * j], pl = sip[2 * j + 1];
+      const dw dx = sub_pos(T.x, dw{ph.x, pl.x}), dy = sub_pos(T.y, dw{ph.y, pl.y}), dz = sub_pos(T.z, dw{ph.z, pl.z});
+      const dw ir = rsqrt_u(norm2_u(dx, dy, dz));
+      const dw ir2 = mul_u(ir, ir);
+      const dw ir3 = mul_u(ir, ir2);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!(mask >> r & 1u)) continue;
+        const float4 v0 = sis[r][5 * j], v1 = sis[r][5 * j + 1], v2 = sis[r][5 * j + 2], v3 = sis[r][5 * j + 3],
+                     v4 = sis[r][5 * j + 4];
+        const dw fx{v0.x, v2.y}, fy{v0.y, v2.z}, fz{v0.z, v2.w};
+        const dw tx{v0.w, v3.x}, ty{v1.x, v3.y}, tz{v1.y, v3.z};
+        const dw qx{v1.z, v3.w}, qy{v1.w, v4.x}, qz{v2.x, v4.y};
+        // Stokeslet
+        const dw cs = mul_u(dot3_u(dx, dy, dz, fx, fy, fz), ir2);
+        acc_u(T.ux[r], mul_u(ir, add_u(fx, mul_u(cs, dx))));
+        acc_u(T.uy[r], mul_u(ir, add_u(fy, mul_u(cs, dy))));
+        acc_u(T.uz[r], mul_u(ir, add_u(fz, mul_u(cs, dz))));
+        // rotlet (t x r) / r^3
+        acc_u(T.ux[r], mul_u(ir3, add_u(mul_u(ty, dz), neg(mul_u(tz, dy)))));
+        acc_u(T.uy[r], mul_u(ir3, add_u(mul_u(tz, dx), neg(mul_u(tx, dz)))));
+        acc_u(T.uz[r], mul_u(ir3, add_u(mul_u(tx, dy), neg(mul_u(ty, dx)))));
+        // potential dipole -d / r^3 + 3 (d.r) r / r^5
+        const dw c3 = times3_u(mul_u(mul_u(dot3_u(dx, dy, dz, qx, qy, qz), ir3), ir2));
+        acc_u(T.ux[r], mul_u(c3, dx));
+        acc_u(T.uy[r], mul_u(c3, dy));
+        acc_u(T.uz[r], mul_u(c3, dz));
+        acc_u(T.ux[r], neg(mul_u(ir3, qx)));
+        acc_u(T.uy[r], neg(mul_u(ir3, qy)));
+        acc_u(T.uz[r], neg(mul_u(ir3, qz)));
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T.ux[r] = two_sum(T.ux[r].h, T.ux[r].l);
+      T.uy[r] = two_sum(T.uy[r].h, T.uy[r].l);
+      T.uz[r] = two_sum(T.uz[r].h, T.uz[r].l);
+    }
+  }
+}
+
+// work[b] = (lead problem, tile of the 1-node-per-thread tiling, first index into rhs_prob, count);
+// the sources are split over nparts CTAs per item as in pairs_dw_batch_kernel
+template <int R>
+__global__ void __launch_bounds__(kPairThreads) pairs_dw_multi_kernel(const PairArgs<double>* __restrict__ args,
+                                                                      const int4* __restrict__ work,
+                                                                      const int* __restrict__ rhs_prob,
+                                                                      const int* __restrict__ active, BatchVecs bv,
+                                                                      int nparts) {
+  __shared__ float4 sp[2 * kTileProxyM];
+  __shared__ float4 sf[R][2 * kTileProxyM];
+  __shared__ float4 sip[2 * kTileImgM];
+  __shared__ float4 sis[R][5 * kTileImgM];
+  const int4 w = work[blockIdx.x / nparts];
+  const int part = blockIdx.x % nparts;
+  int prob[R];
+  unsigned mask = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    prob[r] = rhs_prob[w.z + min(r, w.w - 1)];
+    if (r < w.w && active[prob[r]]) mask |= 1u << r;
+  }
+  if (!mask) return;
+  const PairArgs<double> A = args[w.x];
+  const double* lam[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) lam[r] = bv.lam + bv.uoff[prob[r]];
+  const int t = w.y;
+  const int k = A.tile_sphere[t];
+  const int start = A.tile_start[t];
+  const int cnt = A.tile_count[t];
+  CentreShift64 sh;
+  sh.cen = A.cen64;
+  sh.init(k);
+  DWMulti<R> T;
+  {
+    const int idx = threadIdx.x;
+    const int node = start + (idx < cnt ? idx : cnt - 1);
+    const D4 p = A.tgt[node];
+    T.x = dw_split(p.x);
+    T.y = dw_split(p.y);
+    T.z = dw_split(p.z);
+#pragma unroll
+    for (int r = 0; r < R; ++r) T.ux[r] = T.uy[r] = T.uz[r] = dw{0.f, 0.f};
+  }
+  const int total = A.P * A.N;
+  const int p_lo = k < 0 ? total : k * A.N, p_w = k < 0 ? 0 : A.N;
+  const long long p_eff = total - p_w;
+  const int pe0 = (int)(p_eff * part / nparts), pe1 = (int)(p_eff * (part + 1) / nparts);
+  dwm_proxy_range<R>(A, sh, k, lam, mask, min(pe0, p_lo), min(pe1, p_lo), sp, sf, T);
+  dwm_proxy_range<R>(A, sh, k, lam, mask, max(pe0, p_lo) + p_w, max(pe1, p_lo) + p_w, sp, sf, T);
+  const int i_lo = k >= 0 ? A.img_off[k] : 0, i_w = k >= 0 ? A.img_off[k + 1] - i_lo : 0;
+  const long long i_eff = A.n_img - i_w;
+  const int ie0 = (int)(i_eff * part / nparts), ie1 = (int)(i_eff * (part + 1) / nparts);
+  dwm_image_range<R>(A, sh, k, lam, mask, min(ie0, i_lo), min(ie1, i_lo), sip, sis, T);
+  dwm_image_range<R>(A, sh, k, lam, mask, max(ie0, i_lo) + i_w, max(ie1, i_lo) + i_w, sip, sis, T);
+  const int idx = threadIdx.x;
+  if (idx >= cnt) return;
+  const long long node = start + idx;
+  const double sw = A.tgt[node].w;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (!(mask >> r & 1u)) continue;
+    const double gx = dw_join(T.ux[r]) * A.scale, gy = dw_join(T.uy[r]) * A.scale, gz = dw_join(T.uz[r]) * A.scale;
+    const long long off = bv.voff[prob[r]];
+    if (nparts > 1) {
+      double* o = bv.partial + off + part * bv.pstride + 3 * node;
+      o[0] = gx;
+      o[1] = gy;
+      o[2] = gz;
+    } else {
+      const double* mu = bv.mu + off;
+      double* out = bv.out + off;
+      out[3 * node] = mu[3 * node] + sw * gx;
+      out[3 * node + 1] = mu[3 * node + 1] + sw * gy;
+      out[3 * node + 2] = mu[3 * node + 2] + sw * gz;
+    }
+  }
+}
+
 // the batched counterpart of pair_parts_reduce_kernel: CTA (chunk of an active problem, piece of
 // blockDim elements), so that a single short problem still gets enough CTAs
 __global__ void pair_parts_reduce_batch_kernel(SegTable t, const PairArgs<double>* __restrict__ args, BatchVecs bv,
@@ -1929,7 +2178,8 @@ void fill_pair_args64(void* host_dst, const TargetSet& tg, const SourceSet& src,
 void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_work, int n_work, const int* d_active,
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
-                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen) {
+                          long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen,
+                          bool skip_reduce) {
   if (n_work == 0) return;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args);
   BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
@@ -1940,7 +2190,7 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
     } else {
       if (!partial) parts = 1;
       pairs_dw_batch_kernel<1><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_active, bv, parts);
-      if (parts > 1) {
+      if (parts > 1 && !skip_reduce) {
         ++t_launches;
         if (seg_ctas(seg) > 0)
           pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), (seg.chunk + 127) / 128), 128, 0, st>>>(seg, args, bv, parts);
@@ -1950,6 +2200,28 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
     if (nodes_per_thread == 4) pairs_batch_kernel<double, 4><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
     else pairs_batch_kernel<double, 1><<<n_work, kPairThreads, 0, st>>>(args, d_work, d_active, bv);
   }
+}
+
+void launch_pairs_multi64(const void* d_args1, const int4* d_work, int n_work, const int* d_rhs, const int* d_active,
+                          const double* lam, const double* mu, double* out, const long long* d_uoff,
+                          const long long* d_voff, int parts, double* partial, long long pstride,
+                          const long long* d_nlen, cudaStream_t st) {
+  if (n_work == 0) return;
+  if (!partial) parts = 1;
+  const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args1);
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
+  ++t_launches;
+  pairs_dw_multi_kernel<kPairRhs><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_rhs, d_active, bv, parts);
+}
+
+void launch_pair_parts_reduce_batch(const void* d_args1, const SegTable& seg, const double* lam, const double* mu,
+                                    double* out, const long long* d_uoff, const long long* d_voff, int parts,
+                                    double* partial, long long pstride, const long long* d_nlen, cudaStream_t st) {
+  if (parts <= 1 || seg_ctas(seg) == 0) return;
+  const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args1);
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
+  ++t_launches;
+  pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), (seg.chunk + 127) / 128), 128, 0, st>>>(seg, args, bv, parts);
 }
 
 void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv, const double* w, double* partial,

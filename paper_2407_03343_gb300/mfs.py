@@ -68,7 +68,8 @@ class Timing(C.Structure):
                 ("by_kind_proxy", C.c_longlong * 3), ("by_kind_image_nodes", C.c_longlong * 3),
                 ("krylov_launches", C.c_longlong), ("krylov_ms", C.c_double), ("krylov_bytes", C.c_double),
                 ("far_launches", C.c_longlong), ("far_ms", C.c_double), ("far_pairs", C.c_longlong),
-                ("tc_launches", C.c_longlong), ("tc_columns", C.c_longlong)]
+                ("tc_launches", C.c_longlong), ("tc_columns", C.c_longlong),
+                ("pair_issued_flops", C.c_double), ("pair_shared_rhs", C.c_longlong)]
 
 
 class PairShapes(C.Structure):

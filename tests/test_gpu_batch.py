@@ -100,3 +100,44 @@ def test_repeated_contexts_device_buffers(problems):
     for (F, T), f, t in zip(outs, dF, dT):
         ref = np.abs(np.r_[F.ravel(), T.ravel()]).max()
         assert np.abs(f.cpu().numpy() - F).max() <= 1e-9 * ref and np.abs(t.cpu().numpy() - T).max() <= 1e-9 * ref
+
+
+def test_batch_of_64_problems_up_to_256_spheres():
+    # the shape of the batched workload (64 independent suspensions, sphere counts from 2 to 256,
+    # gaps of attached spheres log-uniform in [1e-3, 1e-1]) at a reduced discretisation: 63
+    # suspensions with 2 to 12 spheres and one of 256 spheres (a dilute lattice with three
+    # near-contact pairs, so most of its spheres share the basic factor and run step 1 on the
+    # tensor cores).  The MIXED batch must reproduce one-by-one solves of a sample of its problems
+    # to the accuracy their residual allows: both reach 1e-8 (the MIXED floor at this
+    # discretisation is ~1.6e-9), and the forces of the gap-2e-3 pair amplify a residual
+    # difference ~1/gap (measured 3.3e-5 of the largest force), hence 1e-4 there and 1e-5 elsewhere.
+    kw = dict(n_proxy=96, r_proxy=0.63, m_basic=200)
+    cents = workloads.batch(n_problems=63, seed=9, p_lo=2, p_hi=12)
+    g = np.arange(8) * 3.0
+    big = np.array([[x, y, z] for x in g for y in g for z in g[:4]])
+    for i, gap in enumerate((2e-3, 2e-2, 8e-2)):
+        big[4 * i + 1] = big[4 * i] + np.array([0.0, 0.0, 2.0 + gap])  # bring a neighbour close
+    cents.append(big)
+    assert big.shape[0] == 256 and max(c.shape[0] for c in cents) == 256
+    ctxs = []
+    try:
+        for c in cents:
+            ctx = mfs.Context(0)
+            ctx.set_spheres(c)
+            ctx.build(**kw)
+            ctxs.append(ctx)
+        assert ctxs[-1].sizes().n_contacts == 3
+        vel = [workloads.rigid_velocities(c.shape[0], seed=300 + i) for i, c in enumerate(cents)]
+        for ctx, (v, w) in zip(ctxs, vel):
+            ctx.set_rigid_velocities(v, w)
+        infos = mfs.batch_solve(ctxs, precision="mixed", tol=1e-8)
+        assert len(infos) == 64 and all(i.converged == 1 and i.rel_residual <= 1e-8 for i in infos)
+        batched = [ft(c) for c in ctxs]
+        for i in (0, 17, 40, 62, 63):
+            ctxs[i].set_rigid_velocities(*vel[i])
+            assert ctxs[i].solve(precision="mixed", tol=1e-8).converged
+            fs = ft(ctxs[i])
+            assert np.abs(batched[i] - fs).max() <= (1e-4 if i == 63 else 1e-5) * np.abs(fs).max(), i
+    finally:
+        for ctx in ctxs:
+            ctx.close()
