@@ -44,10 +44,11 @@ FLOPS_ALG = (28.0, 63.0)
 # per image triple (436, 108 FMAs).  Their rate against the FP32 peak is `issue_frac`, a
 # measure of how busy the pipes are, not of algorithmic throughput.
 FLOPS_ISSUED_DW = (248.0, 544.0)
-# dram__bytes_read.sum + dram__bytes_write.sum of one pairs_dw_batch_kernel<1> launch over the 18
-# gap-sweep problems (ncu --set full on `bench.py --kernel-case 20`; 5.05 MB read, 0 written):
-# the kernel is FP32-issue-bound and its operands stay in L2
-PAIR_DW_TRAFFIC_BYTES = 5.055e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one pairs_dw_multi_kernel<3> launch over three
+# gap-sweep geometries with their three motions each (ncu --set full on
+# `bench.py --profile-case gemv_rhs`; 0.94 MB read, 0 written): the kernel is FP32-issue-bound
+# and its operands stay in L2 (the single-problem kernel: 5.05 MB for an 18-problem launch)
+PAIR_DW_TRAFFIC_BYTES = 0.940e6
 
 
 def parse():
@@ -684,7 +685,7 @@ def main():
                                      "image_node_pairs": k_image / max(k_launch, 1)},
                 # dram read + write of one captured launch (ncu, 18 gap-sweep problems, see profiles/)
                 "traffic": PAIR_DW_TRAFFIC_BYTES if prec == "mixed" else None,
-                "traffic_launch": "pairs_dw_batch_kernel<1>, 18-problem launch of --kernel-case 20"
+                "traffic_launch": "pairs_dw_multi_kernel<3>, 9-problem launch of --profile-case gemv_rhs"
                 if prec == "mixed" else None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x median SM clock under load"
                 if prec == "mixed" else "FP64 DFMA probe (mfs_probe_alu_peak)",
