@@ -771,6 +771,7 @@ struct BatchPlan {
   int* rhs_pin = nullptr;
   int2* d_swork1 = nullptr;
   int2* swork_pin = nullptr;
+  unsigned* d_pcount = nullptr;  // per pair-kernel work item: arrivals of its source parts
   int n_mwork = 0, n_swork1 = 0;
   size_t mwork_cap = 0;
   std::vector<int> rhs_shared;             // per problem: right-hand sides in its pair-kernel item
@@ -1007,7 +1008,8 @@ mfs_status make_plan(mfs_ctx* c0, int K, mfs_ctx* const* ctxs, const std::vector
   }
   B->mwork_cap = std::max<size_t>(1, B->w1_host.size());
   ok = ok && (B->d_mwork = B->alloc<int4>(B->mwork_cap)) && (B->d_rhs = B->alloc<int>(K)) &&
-       (B->d_swork1 = B->alloc<int2>(B->mwork_cap)) &&
+       (B->d_swork1 = B->alloc<int2>(B->mwork_cap)) && (B->d_pcount = B->alloc<unsigned>(B->mwork_cap)) &&
+       cudaMemset(B->d_pcount, 0, sizeof(unsigned) * B->mwork_cap) == cudaSuccess &&
        cudaMallocHost(&B->mwork_pin, sizeof(int4) * B->mwork_cap) == cudaSuccess &&
        cudaMallocHost(&B->rhs_pin, sizeof(int) * K) == cudaSuccess &&
        cudaMallocHost(&B->swork_pin, sizeof(int2) * B->mwork_cap) == cudaSuccess;
@@ -1115,6 +1117,7 @@ struct BatchRun {
   bool dw;
   bool fast_a;           // with dw: Sigma^+ U^T from its FP32 copy
   std::vector<int> act;  // host copy of the active flags
+  bool x2_ready = false;  // with dw: the apply's input already split into B->x2 (by the scaling)
 };
 
 // Active flags and the compacted pair work lists of the active problems.
@@ -1219,7 +1222,7 @@ void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
   BatchPlan* B = R.B;
   timed(c, c->ev_gemv, [&] {
     if (R.dw) {
-      launch_split_dw(B->n_total, in, B->x2, R.st);
+      if (!R.x2_ready) launch_split_dw(B->n_total, in, B->x2, R.st);
       if (R.fast_a) {
         launch_gemv_f32_dw(B->gA32, B->x2, B->t2, R.st);
         if (B->tc_nact > 0) {
@@ -1252,18 +1255,17 @@ void batch_apply_kernels(BatchRun& R, const double* in, double* out) {
       // run the 1-node-per-thread kernel with the same source split, one reduction for both
       const long long items = (long long)B->n_mwork + B->n_swork1;
       const int mparts = min_others > 0 ? pair_split_parts(items, min_others, kPairMaxParts) : 1;
+      // (with split sources the last CTA of each item adds the parts)
       launch_pairs_multi64(B->d_args1, B->d_mwork, B->n_mwork, B->d_rhs, B->d_active, B->lh, in, out, B->d_uoff,
-                           B->d_voff, mparts, B->pparts, B->n_total, B->d_nlen, R.st);
+                           B->d_voff, mparts, B->pparts, B->n_total, B->d_nlen, R.st, B->d_pcount);
       launch_pairs_batch64(true, B->d_args1, B->d_swork1, B->n_swork1, B->d_active, 1, B->lh, in, out, B->d_uoff,
-                           B->d_voff, mparts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen, true);
-      launch_pair_parts_reduce_batch(B->d_args1, B->seg, B->lh, in, out, B->d_uoff, B->d_voff, mparts, B->pparts,
-                                     B->n_total, B->d_nlen, R.st);
+                           B->d_voff, mparts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen, true, B->d_pcount);
     } else if (nt == 4)
       launch_pairs_batch64(R.dw, B->d_args, B->d_cwork, B->n_cwork, B->d_active, 4, B->lh, in, out, B->d_uoff,
                            B->d_voff, 1, nullptr, 0, B->seg, R.st);
     else
       launch_pairs_batch64(R.dw, B->d_args1, B->d_cwork1, B->n_cwork1, B->d_active, 1, B->lh, in, out, B->d_uoff,
-                           B->d_voff, parts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen);
+                           B->d_voff, parts, B->pparts, B->n_total, B->seg, R.st, B->d_nlen, false, B->d_pcount);
   });
   // mobility problems: the rigid motion of the border unknowns, and their force/torque rows
   // (the bordered operator of the single solves, problem by problem)
@@ -1448,7 +1450,9 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
   CUDA_TRY(c, cudaMemsetAsync(S.iters, 0, sizeof(int) * K, R.st));
   CUDA_TRY(c, cudaMemsetAsync(S.jused, 0, sizeof(int) * K, R.st));
   CUDA_TRY(c, cudaMemsetAsync(S.err, 0, sizeof(int), R.st));
-  launch_seg_scale(B->seg, B->scl, b, V, R.st);
+  // v_0 = b / ||b||, split for the first double-float apply at the same time
+  if (R.dw) launch_seg_scale_split(B->seg, B->scl, b, V, B->x2, R.st);
+  else launch_seg_scale(B->seg, B->scl, b, V, R.st);
   double* h1 = B->hbuf;
   double* h2 = B->hbuf + (size_t)kMaxBatchVec * K;
   double* hn = B->hbuf + (size_t)2 * kMaxBatchVec * K;
@@ -1459,7 +1463,9 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
   for (int j = 0; j < restart && used < iter_budget && any; ++j) {
     last_j = j;
     double* w = V + (size_t)(j + 1) * n;
+    R.x2_ready = R.dw;
     batch_apply_kernels(R, V + (size_t)j * n, w);
+    R.x2_ready = false;
     timed(c, c->ev_krylov, [&] {
       launch_seg_dots(B->seg, j + 1, V, n, w, B->partial, h1, R.st);
       launch_seg_update(B->seg, j + 1, V, n, h1, -1.0, w, R.st);
@@ -1468,7 +1474,9 @@ mfs_status batch_gmres_cycle(BatchRun& R, const double* b, double* x, const std:
     });
     launch_seg_dots(B->seg, 1, w, n, w, B->partial, hn, R.st);
     launch_batch_givens(S, j, h1, h2, hn, R.st);
-    launch_seg_scale(B->seg, B->scl, w, w, R.st);
+    // v_{j+1} = w / h_{j+1,j}, split for the next apply
+    if (R.dw) launch_seg_scale_split(B->seg, B->scl, w, w, B->x2, R.st);
+    else launch_seg_scale(B->seg, B->scl, w, w, R.st);
     CHECK_LAUNCH(c);
     CUDA_TRY(c, cudaMemcpyAsync(B->snap + (size_t)in_window * K, B->d_active, sizeof(int) * K, cudaMemcpyDeviceToHost,
                                 R.st));

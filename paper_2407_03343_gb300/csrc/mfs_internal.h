@@ -188,16 +188,17 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
                           long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen = nullptr,
-                          bool skip_reduce = false);
+                          bool skip_reduce = false, unsigned* d_counter = nullptr);
 // Several right-hand sides on one geometry (double-float, 1 node per thread): work[b] = (lead
 // problem, tile, first index into rhs_prob, count <= kPairRhs); each pair's Green's function is
 // formed once for all of the item's right-hand sides.  parts > 1 writes partial sums as
-// launch_pairs_batch64 does; the caller then runs launch_pair_parts_reduce_batch once.
+// launch_pairs_batch64 does; with d_counter (zeros, one per item) the last CTA of each item adds
+// them, else the caller runs launch_pair_parts_reduce_batch once.
 constexpr int kPairRhs = 3;
 void launch_pairs_multi64(const void* d_args1, const int4* d_work, int n_work, const int* d_rhs, const int* d_active,
                           const double* lam, const double* mu, double* out, const long long* d_uoff,
                           const long long* d_voff, int parts, double* partial, long long pstride,
-                          const long long* d_nlen, cudaStream_t st);
+                          const long long* d_nlen, cudaStream_t st, unsigned* d_counter = nullptr);
 void launch_pair_parts_reduce_batch(const void* d_args1, const SegTable& seg, const double* lam, const double* mu,
                                     double* out, const long long* d_uoff, const long long* d_voff, int parts,
                                     double* partial, long long pstride, const long long* d_nlen, cudaStream_t st);
@@ -277,6 +278,10 @@ void launch_seg_dots(const SegTable& t, int nvec, const double* V, long long ldv
 void launch_seg_update(const SegTable& t, int nvec, const double* V, long long ldv, const double* coef, double sign,
                        double* w, cudaStream_t st);
 void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st);
+// the same scaling, also writing the (hi, lo) float split of the result to x2 (the input of the
+// next double-float apply, which then skips its own split)
+void launch_seg_scale_split(const SegTable& t, const double* s, const double* in, double* out, float2* x2,
+                            cudaStream_t st);
 void launch_axpy64(long long n, double a, const double* x, double* y, cudaStream_t st);
 
 // Device-resident GMRES state of a lockstep batch of K problems: per problem `restart`

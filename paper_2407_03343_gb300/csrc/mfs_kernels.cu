@@ -1018,7 +1018,35 @@ struct BatchVecs {
   double* partial;     // split sources: nparts slices of the concatenated vector length
   long long pstride;
   const long long* nlen;  // node rows (3 n_colloc) of each problem; a mobility problem's border follows
+  unsigned* counter;      // optional, zeros, one per work item: with split sources the last CTA of an
+                          // item adds the parts (in part order) itself and re-arms its counter
 };
+
+// Split sources, fused reduction: every CTA of work item `item` has written its partial sums of the
+// tile's nodes; the last one to arrive adds the parts in part order and writes out = mu + sqrt(w) s.
+// Returns whether this CTA was the last (all threads see the same answer).
+__device__ __forceinline__ bool parts_last_arrival(unsigned* counter, int item, int nparts) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(&counter[item], 1u) == (unsigned)nparts - 1;
+    if (last) counter[item] = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+__device__ __forceinline__ void parts_finish_node(const D4* tgt, long long node, int nparts, const double* partial,
+                                                  long long pstride, const double* mu, double* out) {
+  const double sw = tgt[node].w;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double sum = 0.0;
+    for (int q = 0; q < nparts; ++q) sum += __ldcg(&partial[q * pstride + 3 * node + c]);
+    out[3 * node + c] = mu[3 * node + c] + sw * sum;
+  }
+}
 template <typename T, int NT>
 __global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArgs<T>* __restrict__ args,
                                                                    const int2* __restrict__ work,
@@ -1031,8 +1059,10 @@ __global__ void __launch_bounds__(kPairThreads) pairs_batch_kernel(const PairArg
   A.out = bv.out + bv.voff[w.x];
   pair_tile<T, NT>(A, w.y);
 }
+// (register bounds as the compiler chose them before the fused reduction: 7 CTAs per SM for 1 node
+// per thread, 4 for 4)
 template <int NT>
-__global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const PairArgs<double>* __restrict__ args,
+__global__ void __launch_bounds__(kPairThreads, NT == 1 ? 7 : 4) pairs_dw_batch_kernel(const PairArgs<double>* __restrict__ args,
                                                                       const int2* __restrict__ work,
                                                                       const int* __restrict__ active, BatchVecs bv,
                                                                       int nparts) {
@@ -1043,6 +1073,13 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_batch_kernel(const Pair
   A.mu = bv.mu + bv.voff[w.x];
   A.out = bv.out + bv.voff[w.x];
   pair_tile_dw<NT>(A, w.y, blockIdx.x % nparts, nparts, bv.partial + bv.voff[w.x], bv.pstride);
+  if constexpr (NT == 1) {  // only the 1-node tiling splits sources
+    if (nparts > 1 && bv.counter && parts_last_arrival(bv.counter, blockIdx.x / nparts, nparts)) {
+      const int start = A.tile_start[w.y], cnt = A.tile_count[w.y];
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        parts_finish_node(A.tgt, start + i, nparts, bv.partial + bv.voff[w.x], bv.pstride, A.mu, A.out);
+    }
+  }
 }
 // ------------------------------------------------------------------ several right-hand sides on one geometry
 // The problems of a batch that share a context (the motions of one geometry) have the same
@@ -1270,25 +1307,35 @@ __global__ void __launch_bounds__(kPairThreads) pairs_dw_multi_kernel(const Pair
   dwm_image_range<R>(A, sh, k, lam, mask, min(ie0, i_lo), min(ie1, i_lo), sip, sis, T);
   dwm_image_range<R>(A, sh, k, lam, mask, max(ie0, i_lo) + i_w, max(ie1, i_lo) + i_w, sip, sis, T);
   const int idx = threadIdx.x;
-  if (idx >= cnt) return;
-  const long long node = start + idx;
-  const double sw = A.tgt[node].w;
+  if (idx < cnt) {
+    const long long node = start + idx;
+    const double sw = A.tgt[node].w;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (!(mask >> r & 1u)) continue;
-    const double gx = dw_join(T.ux[r]) * A.scale, gy = dw_join(T.uy[r]) * A.scale, gz = dw_join(T.uz[r]) * A.scale;
-    const long long off = bv.voff[prob[r]];
-    if (nparts > 1) {
-      double* o = bv.partial + off + part * bv.pstride + 3 * node;
-      o[0] = gx;
-      o[1] = gy;
-      o[2] = gz;
-    } else {
-      const double* mu = bv.mu + off;
-      double* out = bv.out + off;
-      out[3 * node] = mu[3 * node] + sw * gx;
-      out[3 * node + 1] = mu[3 * node + 1] + sw * gy;
-      out[3 * node + 2] = mu[3 * node + 2] + sw * gz;
+    for (int r = 0; r < R; ++r) {
+      if (!(mask >> r & 1u)) continue;
+      const double gx = dw_join(T.ux[r]) * A.scale, gy = dw_join(T.uy[r]) * A.scale, gz = dw_join(T.uz[r]) * A.scale;
+      const long long off = bv.voff[prob[r]];
+      if (nparts > 1) {
+        double* o = bv.partial + off + part * bv.pstride + 3 * node;
+        o[0] = gx;
+        o[1] = gy;
+        o[2] = gz;
+      } else {
+        const double* mu = bv.mu + off;
+        double* out = bv.out + off;
+        out[3 * node] = mu[3 * node] + sw * gx;
+        out[3 * node + 1] = mu[3 * node + 1] + sw * gy;
+        out[3 * node + 2] = mu[3 * node + 2] + sw * gz;
+      }
+    }
+  }
+  if (nparts > 1 && bv.counter && parts_last_arrival(bv.counter, blockIdx.x / nparts, nparts)) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!(mask >> r & 1u)) continue;
+      const long long off = bv.voff[prob[r]];
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+        parts_finish_node(A.tgt, start + i, nparts, bv.partial + off, bv.pstride, bv.mu + off, bv.out + off);
     }
   }
 }
@@ -1712,6 +1759,20 @@ __global__ void seg_scale_kernel(SegTable t, const double* __restrict__ s, const
   if (!t.active[p]) return;
   const double f = s[p];
   for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) out[e] = f * in[e];
+}
+
+__global__ void seg_scale_split_kernel(SegTable t, const double* __restrict__ s, const double* __restrict__ in,
+                                       double* __restrict__ out, float2* __restrict__ x2) {
+  const int b = seg_chunk(t);
+  const int p = t.prob[b];
+  if (!t.active[p]) return;
+  const double f = s[p];
+  for (long long e = t.start[b] + threadIdx.x; e < t.end[b]; e += blockDim.x) {
+    const double v = f * in[e];
+    out[e] = v;
+    const dw d = dw_split(v);
+    x2[e] = make_float2(d.h, d.l);
+  }
 }
 
 __global__ void axpy64_kernel(long long n, double a, const double* __restrict__ x, double* __restrict__ y) {
@@ -2179,10 +2240,11 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
                           int nodes_per_thread, const double* lam, const double* mu, double* out,
                           const long long* d_uoff, const long long* d_voff, int parts, double* partial,
                           long long pstride, const SegTable& seg, cudaStream_t st, const long long* d_nlen,
-                          bool skip_reduce) {
+                          bool skip_reduce, unsigned* d_counter) {
   if (n_work == 0) return;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args);
-  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen, d_counter};
+  if (d_counter) skip_reduce = true;  // the last CTA of each item adds the parts
   ++t_launches;
   if (double_float) {
     if (nodes_per_thread == 4) {
@@ -2205,11 +2267,11 @@ void launch_pairs_batch64(bool double_float, const void* d_args, const int2* d_w
 void launch_pairs_multi64(const void* d_args1, const int4* d_work, int n_work, const int* d_rhs, const int* d_active,
                           const double* lam, const double* mu, double* out, const long long* d_uoff,
                           const long long* d_voff, int parts, double* partial, long long pstride,
-                          const long long* d_nlen, cudaStream_t st) {
+                          const long long* d_nlen, cudaStream_t st, unsigned* d_counter) {
   if (n_work == 0) return;
   if (!partial) parts = 1;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args1);
-  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen, d_counter};
   ++t_launches;
   pairs_dw_multi_kernel<kPairRhs><<<n_work * parts, kPairThreads, 0, st>>>(args, d_work, d_rhs, d_active, bv, parts);
 }
@@ -2219,7 +2281,7 @@ void launch_pair_parts_reduce_batch(const void* d_args1, const SegTable& seg, co
                                     double* partial, long long pstride, const long long* d_nlen, cudaStream_t st) {
   if (parts <= 1 || seg_ctas(seg) == 0) return;
   const PairArgs<double>* args = static_cast<const PairArgs<double>*>(d_args1);
-  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen};
+  BatchVecs bv{lam, mu, out, d_uoff, d_voff, partial, pstride, d_nlen, nullptr};
   ++t_launches;
   pair_parts_reduce_batch_kernel<<<dim3(seg_ctas(seg), (seg.chunk + 127) / 128), 128, 0, st>>>(seg, args, bv, parts);
 }
@@ -2241,6 +2303,12 @@ void launch_seg_update(const SegTable& t, int nvec, const double* V, long long l
   ++t_launches;
   seg_update_kernel<<<dim3(seg_ctas(t), (t.chunk + kSegUpdSub - 1) / kSegUpdSub), kSegUpdSub * kSegUpdGroups, 0, st>>>(
       t, nvec, V, ldv, coef, sign, w);
+}
+void launch_seg_scale_split(const SegTable& t, const double* s, const double* in, double* out, float2* x2,
+                            cudaStream_t st) {
+  if (seg_ctas(t) == 0) return;
+  ++t_launches;
+  seg_scale_split_kernel<<<seg_ctas(t), kSegThreads, 0, st>>>(t, s, in, out, x2);
 }
 void launch_seg_scale(const SegTable& t, const double* s, const double* in, double* out, cudaStream_t st) {
   if (seg_ctas(t) == 0) return;
